@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Benchmark: half-stored M-scheme Hamiltonian nonzeros built per second.
+
+One step = the whole construction path on one synthetic workload: basis
+enumeration (sub-determinants, partner ranges, neighbour lists), the count
+pass, the row-pointer scan and the fill pass (columns and values), with the
+two-body table already resident in HBM.  value = nonzeros of all ranks'
+steps / device time of those steps.  L2 is flushed (a 256 MiB write) between
+timed steps.
+
+Default workload: 4 protons + 4 neutrons, Nmax = 6, 2M = 0, one seeded
+synthetic two-body table (PCG64 seed 0, N(0,1) float32 per entry): dimension
+2,217,754, 924,863,410 stored nonzeros.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank builds the same workload on its own GPU
+(replicas, weak scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hamiltonian nonzeros built/sec (% HBM roofline); gradient/forward time ratio"
+WORKLOADS = {
+    "4p4n_nmax6": dict(Z=4, N=4, Nmax=6, twoM=0, seed=0),
+    "3p3n_nmax6": dict(Z=3, N=3, Nmax=6, twoM=0, seed=100),
+    "4p4n_nmax4": dict(Z=4, N=4, Nmax=4, twoM=0, seed=0),
+    "3p3n_nmax2": dict(Z=3, N=3, Nmax=2, twoM=0, seed=0),
+}
+FALLBACK_HBM_GBS = 6800.0
+BYTES_PER_NNZ = 8            # int32 column + float32 value written by the fill
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="4p4n_nmax6", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=3000, help="rows in the oracle's timed sample")
+    return ap.parse_args()
+
+
+def workload_name(w):
+    return f"{w['Z']}p{w['N']}n_nmax{w['Nmax']}_2M{w['twoM']}_plain_build_seed{w['seed']}"
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def fill_traffic(fill_source_sha):
+    """DRAM bytes per fill launch from the committed ncu summary, if it was taken
+    on the current fill kernel (same source hash); else None."""
+    p = os.path.join(ROOT, "profiles", "fill_4p4n_nmax6.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != fill_source_sha:
+        return None
+    return float(m.group(1))
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("ham.cu", "cih_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1412_5989_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rate(w, rows_n, seed=1):
+    """The CPU oracle, as it stands, on a bounded sample of rows of the same
+    workload: (nnz/s, nnz in sample, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_1412_5989_gb300 import synth
+    S = oracle.Space(w["Z"], w["N"], w["Nmax"], w["twoM"])
+    t = synth.tbme_table(S.tbme_len, w["seed"])
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(S.dim, size=min(rows_n, S.dim), replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    cnt, off, col, val = S.rows(rows, t)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return float(cnt.sum()) / dt, int(cnt.sum()), dt, threads, len(rows)
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_rate(w, max(50, args.cpu_rows // 20))
+    rates, times, nnzs = [], [], 0
+    threads = rows = 0
+    for k in range(args.steps):
+        r, n, dt, threads, rows = oracle_rate(w, args.cpu_rows // 4, seed=10 + k)
+        rates.append(r)
+        times.append(dt)
+        nnzs += n
+    value = nnzs / sum(times)
+    sample = (f"{rows} random rows per step (of {args.workload}), count + fill by the oracle's plain "
+              f"row walk, OpenMP over rows")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": workload_name(w), "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1412_5989_gb300 import cih, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    st = torch.cuda.current_stream()
+    w = WORKLOADS[args.workload]
+    sp = (w["Z"], w["N"], w["Nmax"], w["twoM"])
+
+    B0 = cih.Basis(*sp)
+    dim, tl = B0.dim, B0.tbme_len
+    tbme_h = synth.tbme_table(tl, w["seed"])
+    tbme = torch.from_numpy(tbme_h).to(dev)
+    rowptr, nnz = B0.count()
+    col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    val = torch.empty((1, max(nnz, 1)), dtype=torch.float32, device=dev)
+    B0.close()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(ev):
+        ev[0].record(st)
+        B = cih.Basis(*sp)                                   # basis + neighbour lists
+        ev[1].record(st)
+        B.count_into(rowptr)                                 # count + scan
+        ev[2].record(st)
+        B.fill(rowptr, nnz, tbme, col=col, val=val)          # fill: columns + values
+        ev[3].record(st)
+        return B
+
+    def new_events(n=4):
+        return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+    for _ in range(args.warmup):
+        B = step(new_events())
+        torch.cuda.synchronize()
+        B.check()
+        B.close()
+    assert int(rowptr[-1].item()) == nnz
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    launches0 = cih.kernel_launches()
+    t_step, t_basis, t_count, t_fill = [], [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1)                                        # evict L2 between steps (not timed)
+        ev = new_events()
+        B = step(ev)
+        torch.cuda.synchronize()
+        t_step.append(ev[0].elapsed_time(ev[3]))
+        t_basis.append(ev[0].elapsed_time(ev[1]))
+        t_count.append(ev[1].elapsed_time(ev[2]))
+        t_fill.append(ev[2].elapsed_time(ev[3]))
+        B.close()
+    launches = cih.kernel_launches() - launches0
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(t_step)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        torch.distributed.barrier()
+    value = world * args.steps * nnz / (total_ms * 1e-3)
+
+    # gradient / forward time ratio: adjoint over the same structure with a
+    # normalised vector, against the fill pass
+    Bg = cih.Basis(*sp)
+    Bg.count_into(rowptr)
+    psi = torch.rand(dim, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    psi /= psi.norm()
+    Bg.tbme_grad(rowptr, psi)
+    torch.cuda.synchronize()
+    tg = []
+    for _ in range(max(1, min(args.steps, 3))):
+        a, b = new_events(2)
+        a.record(st)
+        Bg.tbme_grad(rowptr, psi)
+        b.record(st)
+        torch.cuda.synchronize()
+        tg.append(a.elapsed_time(b))
+    Bg.close()
+    grad_ratio = statistics.median(tg) / statistics.median(t_fill)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        tb_pin = torch.from_numpy(tbme_h).pin_memory()
+        col_h = torch.empty(nnz, dtype=torch.int32, pin_memory=True)
+        val_h = torch.empty(nnz, dtype=torch.float32, pin_memory=True)
+        rp_h = torch.empty(dim + 1, dtype=torch.int64, pin_memory=True)
+        te = []
+        for k in range(args.warmup + args.steps):
+            flush.fill_(1)
+            a, b = new_events(2)
+            a.record(st)
+            tbme.copy_(tb_pin, non_blocking=True)
+            B = cih.Basis(*sp)
+            B.count_into(rowptr)
+            B.fill(rowptr, nnz, tbme, col=col, val=val)
+            rp_h.copy_(rowptr, non_blocking=True)
+            col_h.copy_(col[:nnz], non_blocking=True)
+            val_h.copy_(val[0, :nnz], non_blocking=True)
+            b.record(st)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                te.append(a.elapsed_time(b))
+            B.close()
+        e_ms = sum(te) / len(te)
+        if world > 1:
+            tt = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": world * nnz / (e_ms * 1e-3), "unit": "nnz/s",
+               "h2d_bytes_per_step": int(tl * 4),
+               "d2h_bytes_per_step": int(nnz * BYTES_PER_NNZ + (dim + 1) * 8)}
+        del col_h, val_h
+
+    peak, peak_kind = measured_peak()
+    fill_ms = statistics.median(t_fill)
+    achieved = nnz * BYTES_PER_NNZ / (fill_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "kernel": "k_walk<4,1> (fill)", "algorithmic_bytes_per_launch": nnz * BYTES_PER_NNZ,
+                "traffic": fill_traffic(kernel_source_sha())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, n, dt, threads, rows = oracle_rate(w, args.cpu_rows)
+        cpu = {"value": r, "unit": "nnz/s", "cores": threads, "kind": "oracle",
+               "sample": f"{rows} random rows of {args.workload} ({n} nonzeros, {dt:.1f} s): count + fill by "
+                         f"the oracle's plain row walk, OpenMP over rows"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(w), "dim": dim, "nnz_half": nnz, "tbme_entries": tl,
+                       "tbme_sets": 1, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "stages_ms": {"basis": statistics.median(t_basis), "count_scan": statistics.median(t_count),
+                          "fill": fill_ms, "adjoint": statistics.median(tg)},
+            "grad_fwd_ratio": grad_ratio,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

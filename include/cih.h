@@ -1,0 +1,194 @@
+/*
+ * cih.h -- C ABI of libcih: GB300 (sm_103a) construction of the half-stored
+ * M-scheme configuration-interaction Hamiltonian.
+ *
+ * The method is that of arXiv 1412.5989 ("Accelerating Ab Initio Nuclear
+ * Physics Calculations with GPUs"): the nuclear many-body Schroedinger
+ * equation becomes a large sparse symmetric matrix eigenproblem over a basis
+ * of Slater determinants (Sec. 1); its nonzeros are located, computed and
+ * stored, only half of the symmetric matrix being generated (Sec. 2); the
+ * nonzeros are counted in one pass so the arrays can be allocated and then
+ * computed in a second pass (Sec. 4.1), stored in compressed-row form
+ * (Sec. 4.1); and the lowest eigenpairs follow by Lanczos (Sec. 2).
+ *
+ * Conventions (the paper states them in prose only; these are the readings
+ * this library implements, identical to the CPU oracle's):
+ *   - orbitals of a species with Z > 0 particles: harmonic-oscillator states
+ *     (N, l, 2j, 2m) with N <= N_F + Nmax, N_F the highest shell filled by the
+ *     lowest configuration, ordered (N, l, 2j, 2m) ascending; a species with
+ *     no particles has no orbitals.  Combined index: protons 0..n_orb_p-1,
+ *     then neutrons n_orb_p..n_orb_p+n_orb_n-1.
+ *   - sub-determinants of a species: its particle subsets that occur in at
+ *     least one basis state, ordered by (2M, N mod 2, N, bit string read as
+ *     an unsigned multiword integer) ascending.
+ *   - basis: pairs (proton sub-det p, neutron sub-det n) with 2M_p + 2M_n =
+ *     2M, N_p + N_n <= N0 + Nmax and N_p + N_n = N0 + Nmax (mod 2), in
+ *     lexicographic (p, n) order.  Each p's partners form one contiguous range.
+ *   - |Phi> = a+_{i1} ... a+_{iA} |0>, i1 < ... < iA (combined index).
+ *   - H = sum_a e_a a+_a a_a + sum_{a<b, c<d} V_{ab,cd} a+_a a+_b a_d a_c,
+ *     e_a = hbar_omega (N_a + 3/2) unless a per-orbital table is given.
+ *   - stored: the upper triangle j >= i of every (i, j) whose determinants
+ *     differ by at most two particles, whatever the value (so K tables share
+ *     one structure); rows in basis order, columns ascending.
+ *   - two-body table (input format), one set = tbme_len floats: channels pp,
+ *     nn, pn concatenated; a pair (a<b) is in its channel when N_a + N_b <=
+ *     N0 + Nmax - N0(other A-2 particles); pairs grouped by (2M_pair, parity)
+ *     ascending, lexicographic (a, b) inside a group; each group stores its
+ *     packed row-major upper triangle (bra pair index u <= ket pair index v at
+ *     group_offset + u*n - u(u-1)/2 + (v-u)).  One entry stands for V_{ab,cd}
+ *     and V_{cd,ab}; a swapped pair flips the sign.
+ *
+ * Ownership: the caller owns every device array passed in (allocate it with
+ * any allocator, e.g. torch).  The library owns the basis handle and the
+ * device memory behind it (sub-determinant tables, neighbour lists, table
+ * layout, scan scratch).  Every call is ordered on the given CUDA stream
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
+ * that return a host value (nnz_out, evals_host) synchronise that stream.
+ * A handle must not be used by two host threads at once.
+ *
+ * Errors: every call returns 0 or a negative CIH_ERR_* code; no C++ exception
+ * crosses the ABI.  cih_strerror() names a code; cih_last_error_detail()
+ * returns the last failure's message for the calling thread.
+ */
+#ifndef CIH_H
+#define CIH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CIH_OK              0
+#define CIH_ERR_ARG        -1   /* invalid argument or NULL pointer          */
+#define CIH_ERR_NOMEM      -2   /* a library-owned allocation failed         */
+#define CIH_ERR_CAPACITY   -3   /* the result does not fit (e.g. nnz budget) */
+#define CIH_ERR_TIMEOUT    -4   /* a bounded device wait gave up             */
+#define CIH_ERR_UNSUPPORTED -5  /* a size outside what the kernels handle    */
+#define CIH_ERR_CUDA       -6   /* a CUDA runtime call failed                */
+#define CIH_ERR_DEVICE     -7   /* a kernel's own bounds check tripped        */
+
+typedef struct {
+    int32_t Z;      /* protons                                 */
+    int32_t N;      /* neutrons                                */
+    int32_t Nmax;   /* oscillator quanta above the lowest configuration */
+    int32_t twoM;   /* twice the total angular-momentum projection      */
+} cih_space_t;
+
+typedef struct cih_basis *cih_basis_h;
+
+/* Build the many-body basis for *space on the current CUDA device (Sec. 2:
+ * the index tables that define the basis come before the matrix): orbitals,
+ * sub-determinants of both species, partner ranges, row offsets, the
+ * two-body table layout, and the neighbour lists the kernels walk.  Work is
+ * ordered on `stream`; the call returns after the stream has finished it.
+ * *out receives a new handle (release with cih_basis_destroy).
+ * Errors: CIH_ERR_ARG (NULL, Z or N < 0, Nmax < 0), CIH_ERR_UNSUPPORTED
+ * (more than 256 orbitals per species, a dimension above 2^31-1, a
+ * neighbour list longer than the sort tile), CIH_ERR_NOMEM, CIH_ERR_CUDA. */
+int cih_basis_enumerate(const cih_space_t *space, cih_basis_h *out, void *stream);
+
+/* Sizes of a basis.  Any output pointer may be NULL.
+ * dim: basis dimension (rows); n_orb_p / n_orb_n: orbitals per species;
+ * tbme_len[3]: entries of the pp, nn and pn channels (one set's table is
+ * their sum); n_sd[2]: sub-determinants per species. */
+int cih_basis_info(cih_basis_h h, int64_t *dim, int32_t *n_orb_p, int32_t *n_orb_n,
+                   int64_t tbme_len[3], int64_t n_sd[2]);
+
+/* Copy host-side basis tables out (for inspection and tests).  Any pointer
+ * may be NULL.  orbitals: (n_orb_p + n_orb_n) x 4 int32 (N, l, 2j, 2m);
+ * subdet_bits_p / _n: n_sd x 4 uint64 words (bit k = species orbital k);
+ * nbeg / ncnt: per proton sub-det neutron partner range; rowbase: n_sd_p + 1
+ * first-row offsets. */
+int cih_basis_tables(cih_basis_h h, int32_t *orbitals, uint64_t *subdet_bits_p,
+                     uint64_t *subdet_bits_n, int32_t *nbeg, int32_t *ncnt, int64_t *rowbase);
+
+int cih_basis_destroy(cih_basis_h h);
+
+/* Host tables only, no device work: the same basis and table layout as
+ * cih_basis_enumerate, for inspection and for checking the host logic on a
+ * machine without a GPU.  Only cih_basis_info, cih_basis_tables,
+ * cih_tbme_index and cih_basis_destroy accept such a handle; the device
+ * calls return CIH_ERR_ARG.  Errors as cih_basis_enumerate. */
+int cih_basis_host_only(const cih_space_t *space, cih_basis_h *out);
+
+/* Table index of V_{ab,cd} for combined orbitals a, b, c, d in any order
+ * (the layout above): *index = -1 and *sign = 0 when the pairs are not one
+ * table entry, else *sign = +-1 from the pair orders.  Host-side lookup. */
+int cih_tbme_index(cih_basis_h h, int32_t a, int32_t b, int32_t c, int32_t d,
+                   int64_t *index, int32_t *sign);
+
+/* Count pass + scan (Sec. 4.1: a first pass over the nonzeros only counts
+ * them, so that the output arrays can be sized).  Writes the exclusive prefix sum
+ * of the per-row counts of the half-stored structure into rowptr_dev
+ * (device, dim + 1 int64, caller-owned): rowptr[0] = 0, rowptr[dim] = nnz.
+ * If nnz_out != NULL the stream is synchronised and *nnz_out = nnz.
+ * Errors: CIH_ERR_ARG, CIH_ERR_CUDA. */
+int cih_ham_count(cih_basis_h h, int64_t *rowptr_dev, int64_t *nnz_out, void *stream);
+
+/* Fill pass (Sec. 2 and 4.1: the second pass finds each nonzero again,
+ * computes it and stores it): with rowptr_dev from cih_ham_count, write for every stored
+ * nonzero its column (col_dev: nnz int32) and, for each of the K two-body
+ * sets, its value (val_dev: K x nnz float, set-major).
+ *   tbme_dev: K x tbme_len float (device), set-major, layout above;
+ *   e_sp_dev: NULL for e_a = hbar_omega (N_a + 3/2), else (n_orb_p +
+ *             n_orb_n) double one-body energies (device, combined index).
+ * Values are FP64 sums of FP32 table entries, in a fixed order (one-body
+ * terms by orbital, then two-body terms by spectator / pair), rounded once.
+ * Errors: CIH_ERR_ARG (K < 1, NULL arrays), CIH_ERR_CUDA. */
+int cih_ham_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,
+                 const float *tbme_dev, const double *e_sp_dev,
+                 int32_t *col_dev, float *val_dev, void *stream);
+
+/* Lowest eigenpairs by Lanczos (Sec. 2) for each of K matrices sharing one
+ * structure: FP32 half-stored values, FP64 matrix-vector accumulation, FP64
+ * full reorthogonalisation, FP64 tridiagonal eigensolve on the host.
+ *   val_dev: K x nnz float; nev: eigenvalues wanted (<= 64); max_iter:
+ *   Lanczos steps (<= 2048); tol: relative residual bound on the nev Ritz
+ *   pairs; evals_host: K x nev double (host, ascending; NaN where fewer
+ *   converged Ritz values exist); evec0_dev: NULL or K x dim double (device),
+ *   the normalised lowest Ritz vector of each set.
+ * Lanczos vectors (max_iter x dim double per set) are library-allocated for
+ * the duration of the call.  Returns 0, or 1 if some set did not meet tol
+ * within max_iter (results still written), or a CIH_ERR_* code. */
+int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
+                       const float *val_dev, int32_t K, int32_t nev, int32_t max_iter,
+                       double tol, double *evals_host, double *evec0_dev, void *stream);
+
+/* Adjoint: d E0 / d t for every two-body table entry t of each of K sets,
+ * given the normalised lowest eigenvectors psi (Hellmann-Feynman, E0 =
+ * psi^T H psi): g_t = sum over stored (i, j) whose value uses t with sign s of
+ * w * s * psi_i * psi_j, w = 2 off the diagonal and 1 on it.  The sum is
+ * deterministic (fixed-point integer accumulation, 2^-56 resolution).
+ *   psi_dev: K x dim double (device); grad_dev: K x tbme_len double (device,
+ *   caller-owned, overwritten).
+ * Scratch: K x tbme_len int64 library-allocated for the call.
+ * Errors: CIH_ERR_ARG, CIH_ERR_NOMEM, CIH_ERR_CUDA. */
+int cih_ham_tbme_grad(cih_basis_h h, const int64_t *rowptr_dev, int32_t K,
+                      const double *psi_dev, double *grad_dev, void *stream);
+
+/* Synchronise `stream`, read and clear the basis' device error word.
+ * Returns CIH_ERR_DEVICE if a kernel met a pair outside the table layout
+ * (which the walk never produces for a consistent basis), else 0. */
+int cih_check(cih_basis_h h, void *stream);
+
+/* Eigen-decomposition of the symmetric tridiagonal matrix with diagonal
+ * diag[n] and off-diagonal offdiag[n-1] (host arrays; offdiag may be NULL
+ * when n = 1), the host step of cih_lanczos_lowest: implicit QR with
+ * Wilkinson shifts.  evals[n] ascending; evecs (NULL or n x n, row-major)
+ * holds eigenvector k in column k.  Errors: CIH_ERR_ARG, CIH_ERR_NOMEM. */
+int cih_tridiag_eigen(int32_t n, const double *diag, const double *offdiag, double *evals, double *evecs);
+
+/* Number of kernels this library has launched in the process so far (all
+ * devices, all handles): the difference across a region counts the region's
+ * launches.  Errors: CIH_ERR_ARG. */
+int cih_kernel_launches(int64_t *out);
+
+const char *cih_strerror(int code);
+const char *cih_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CIH_H */

@@ -1,0 +1,224 @@
+"""ctypes binding of libcih (include/cih.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; torch only
+provides device memory and the current stream.  Importing this module loads
+``_build/libcih.so`` and raises if it is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcih.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libcih.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                      "or python -m paper_1412_5989_gb300.build")
+
+lib = C.CDLL(LIB_PATH)
+
+_P = C.c_void_p
+_i64p = C.POINTER(C.c_int64)
+_i32p = C.POINTER(C.c_int32)
+_dp = C.POINTER(C.c_double)
+
+
+class Space(C.Structure):
+    _fields_ = [("Z", C.c_int32), ("N", C.c_int32), ("Nmax", C.c_int32), ("twoM", C.c_int32)]
+
+
+_SIGS = {
+    "cih_basis_enumerate": [C.POINTER(Space), C.POINTER(_P), _P],
+    "cih_basis_host_only": [C.POINTER(Space), C.POINTER(_P)],
+    "cih_basis_info": [_P, _i64p, _i32p, _i32p, _i64p, _i64p],
+    "cih_basis_tables": [_P, _i32p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _i32p, _i32p, _i64p],
+    "cih_tbme_index": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _i64p, _i32p],
+    "cih_basis_destroy": [_P],
+    "cih_ham_count": [_P, _P, _i64p, _P],
+    "cih_ham_fill": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
+    "cih_check": [_P, _P],
+    "cih_lanczos_lowest": [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _P, _P],
+    "cih_ham_tbme_grad": [_P, _P, C.c_int32, _P, _P, _P],
+    "cih_tridiag_eigen": [C.c_int32, _dp, _dp, _dp, _dp],
+    "cih_kernel_launches": [_i64p],
+    "cih_strerror": [C.c_int],
+    "cih_last_error_detail": [],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_char_p if _name in ("cih_strerror", "cih_last_error_detail") else C.c_int
+
+EXPORTED = sorted(_SIGS)
+
+
+class CihError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib.cih_strerror(code).decode()
+        detail = lib.cih_last_error_detail().decode()
+        super().__init__(f"{where}: {msg} ({code}): {detail}")
+
+
+def _ok(rc: int, where: str) -> int:
+    if rc < 0:
+        raise CihError(rc, where)
+    return rc
+
+
+def _ptr(t) -> int | None:
+    """Device (or host) address of a tensor / array, or None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def kernel_launches() -> int:
+    """Kernels libcih has launched in this process so far."""
+    n = C.c_int64()
+    _ok(lib.cih_kernel_launches(C.byref(n)), "kernel_launches")
+    return n.value
+
+
+def tridiag_eigen(diag, offdiag):
+    """Eigenvalues (ascending) and eigenvectors (columns) of a symmetric tridiagonal."""
+    d = np.ascontiguousarray(diag, dtype=np.float64)
+    e = np.ascontiguousarray(offdiag, dtype=np.float64)
+    n = len(d)
+    w = np.zeros(n)
+    Z = np.zeros((n, n))
+    _ok(lib.cih_tridiag_eigen(n, d.ctypes.data_as(_dp), e.ctypes.data_as(_dp) if n > 1 else None,
+                              w.ctypes.data_as(_dp), Z.ctypes.data_as(_dp)), "tridiag_eigen")
+    return w, Z
+
+
+class Basis:
+    """A many-body basis (Z protons, N neutrons, Nmax, 2M) owned by libcih."""
+
+    def __init__(self, Z: int, N: int, Nmax: int, twoM: int, *, host_only: bool = False, stream=None):
+        self._h = _P()
+        sp = Space(Z, N, Nmax, twoM)
+        if host_only:
+            _ok(lib.cih_basis_host_only(C.byref(sp), C.byref(self._h)), "basis_host_only")
+        else:
+            _ok(lib.cih_basis_enumerate(C.byref(sp), C.byref(self._h), _stream(stream)), "basis_enumerate")
+        self.Z, self.N, self.Nmax, self.twoM = Z, N, Nmax, twoM
+        self.host_only = host_only
+        dim = C.c_int64()
+        op, on = C.c_int32(), C.c_int32()
+        tl = (C.c_int64 * 3)()
+        nsd = (C.c_int64 * 2)()
+        _ok(lib.cih_basis_info(self._h, C.byref(dim), C.byref(op), C.byref(on), tl, nsd), "basis_info")
+        self.dim = dim.value
+        self.n_orb = (op.value, on.value)
+        self.chan_len = tuple(tl)
+        self.tbme_len = sum(self.chan_len)
+        self.n_sd = tuple(nsd)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.cih_basis_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- host tables ----------------------------------------------------
+    def tables(self):
+        ntot = self.n_orb[0] + self.n_orb[1]
+        orbs = np.zeros((max(ntot, 1), 4), np.int32)
+        bp = np.zeros((max(self.n_sd[0], 1), 4), np.uint64)
+        bn = np.zeros((max(self.n_sd[1], 1), 4), np.uint64)
+        nb = np.zeros(max(self.n_sd[0], 1), np.int32)
+        nc = np.zeros(max(self.n_sd[0], 1), np.int32)
+        rb = np.zeros(self.n_sd[0] + 1, np.int64)
+        _ok(lib.cih_basis_tables(self._h, orbs.ctypes.data_as(_i32p), bp.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                 bn.ctypes.data_as(C.POINTER(C.c_uint64)), nb.ctypes.data_as(_i32p),
+                                 nc.ctypes.data_as(_i32p), rb.ctypes.data_as(_i64p)), "basis_tables")
+        return dict(orbitals=orbs[:ntot], bits_p=bp[: self.n_sd[0]], bits_n=bn[: self.n_sd[1]],
+                    nbeg=nb[: self.n_sd[0]], ncnt=nc[: self.n_sd[0]], rowbase=rb)
+
+    def tbme_index(self, a, b, c, d):
+        idx, sg = C.c_int64(), C.c_int32()
+        _ok(lib.cih_tbme_index(self._h, a, b, c, d, C.byref(idx), C.byref(sg)), "tbme_index")
+        return idx.value, sg.value
+
+    # ---- device passes --------------------------------------------------
+    def count(self, stream=None):
+        """Count pass + scan: (rowptr int64[dim+1] on the device, nnz)."""
+        import torch
+        rowptr = torch.empty(self.dim + 1, dtype=torch.int64, device="cuda")
+        nnz = C.c_int64()
+        _ok(lib.cih_ham_count(self._h, _ptr(rowptr), C.byref(nnz), _stream(stream)), "ham_count")
+        return rowptr, nnz.value
+
+    def count_into(self, rowptr, stream=None):
+        """Count pass + scan into a caller tensor; no host synchronisation."""
+        _ok(lib.cih_ham_count(self._h, _ptr(rowptr), None, _stream(stream)), "ham_count")
+
+    def fill(self, rowptr, nnz: int, tbme, hbar_omega: float = 20.0, e_sp=None, stream=None,
+             col=None, val=None):
+        """Fill pass.  tbme: (K, tbme_len) or (tbme_len,) float32 CUDA tensor.
+        Returns (col int32[nnz], val float32[K, nnz])."""
+        import torch
+        t = tbme if tbme.dim() == 2 else tbme.unsqueeze(0)
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.shape[1] != self.tbme_len:
+            raise ValueError("tbme must be a contiguous float32 CUDA tensor of shape (K, tbme_len)")
+        K = t.shape[0]
+        if col is None:
+            col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        if val is None:
+            val = torch.empty((K, max(nnz, 1)), dtype=torch.float32, device="cuda")
+        if e_sp is not None:
+            e_sp = e_sp.to(device="cuda", dtype=torch.float64).contiguous()
+        _ok(lib.cih_ham_fill(self._h, _ptr(rowptr), K, float(hbar_omega), _ptr(t), _ptr(e_sp),
+                             _ptr(col), _ptr(val), _stream(stream)), "ham_fill")
+        return col[:nnz], val[:, :nnz]
+
+    def check(self, stream=None):
+        _ok(lib.cih_check(self._h, _stream(stream)), "check")
+
+    def lanczos(self, rowptr, col, val, nev: int = 5, max_iter: int = 300, tol: float = 1e-8,
+                want_vectors: bool = True, stream=None):
+        """Lowest nev eigenvalues of each of the K matrices; returns
+        (evals (K, nev) float64 numpy, evec0 (K, dim) float64 CUDA or None, converged)."""
+        import torch
+        v = val if val.dim() == 2 else val.unsqueeze(0)
+        K = v.shape[0]
+        ev = np.zeros((K, nev))
+        vec = torch.empty((K, self.dim), dtype=torch.float64, device="cuda") if want_vectors else None
+        rc = _ok(lib.cih_lanczos_lowest(self._h, _ptr(rowptr), _ptr(col), _ptr(v), K, nev, max_iter, tol,
+                                        ev.ctypes.data_as(_dp), _ptr(vec), _stream(stream)), "lanczos_lowest")
+        return ev, vec, rc == 0
+
+    def tbme_grad(self, rowptr, psi, stream=None):
+        """d E0 / d table entry for each set: (K, tbme_len) float64 CUDA tensor."""
+        import torch
+        p = psi if psi.dim() == 2 else psi.unsqueeze(0)
+        p = p.to(torch.float64).contiguous()
+        K = p.shape[0]
+        g = torch.empty((K, max(self.tbme_len, 1)), dtype=torch.float64, device="cuda")
+        _ok(lib.cih_ham_tbme_grad(self._h, _ptr(rowptr), K, _ptr(p), _ptr(g), _stream(stream)), "ham_tbme_grad")
+        return g[:, : self.tbme_len]
+
+
+def build_hamiltonian(basis: Basis, tbme, hbar_omega: float = 20.0, e_sp=None, stream=None):
+    """Count, scan and fill: (rowptr, col, val, nnz)."""
+    rowptr, nnz = basis.count(stream)
+    col, val = basis.fill(rowptr, nnz, tbme, hbar_omega, e_sp, stream)
+    return rowptr, col, val, nnz

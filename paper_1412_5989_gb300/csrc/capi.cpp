@@ -1,0 +1,258 @@
+// The C ABI declared in include/cih.h: argument checks, error codes, and the
+// order of device steps.  No C++ exception crosses it.
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "cih_internal.h"
+
+namespace cih {
+
+static thread_local std::string g_detail;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int fail(int code, const std::string &msg)
+{
+    g_detail = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    g_detail = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();
+    return CIH_ERR_CUDA;
+}
+
+static void release(cih_basis *b)
+{
+    if (!b) return;
+    int cur = 0;
+    bool switched = false;
+    if (!b->buffers.owned.empty() && cudaGetDevice(&cur) == cudaSuccess && cur != b->device)
+        switched = cudaSetDevice(b->device) == cudaSuccess;
+    for (void *p : b->buffers.owned) cudaFree(p);
+    if (switched) cudaSetDevice(cur);
+    delete b;
+}
+
+template <class Fn>
+static int guarded(Fn &&fn)
+{
+    try {
+        return fn();
+    } catch (const std::bad_alloc &) {
+        return fail(CIH_ERR_NOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(CIH_ERR_ARG, "unexpected host exception");
+    }
+}
+
+}  // namespace cih
+
+using namespace cih;
+
+extern "C" {
+
+int cih_basis_host_only(const cih_space_t *space, cih_basis_h *out)
+{
+    if (!space || !out) return fail(CIH_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    return guarded([&]() -> int {
+        cih_basis *b = new cih_basis;
+        int rc = build_host_basis(*space, *b);
+        if (rc) { release(b); return rc; }
+        *out = b;
+        return CIH_OK;
+    });
+}
+
+int cih_basis_enumerate(const cih_space_t *space, cih_basis_h *out, void *stream)
+{
+    if (!space || !out) return fail(CIH_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    return guarded([&]() -> int {
+        cih_basis *b = new cih_basis;
+        int rc = build_host_basis(*space, *b);
+        if (!rc) {
+            cudaError_t e = cudaGetDevice(&b->device);
+            rc = e == cudaSuccess ? upload_and_build_neighbours(*b, (cudaStream_t)stream)
+                                  : cuda_fail(e, "cudaGetDevice");
+        }
+        if (rc) { release(b); return rc; }
+        *out = b;
+        return CIH_OK;
+    });
+}
+
+int cih_basis_info(cih_basis_h h, int64_t *dim, int32_t *n_orb_p, int32_t *n_orb_n,
+                   int64_t tbme_len[3], int64_t n_sd[2])
+{
+    if (!h) return fail(CIH_ERR_ARG, "NULL handle");
+    if (dim) *dim = h->dim;
+    if (n_orb_p) *n_orb_p = h->s[0].n_orb;
+    if (n_orb_n) *n_orb_n = h->s[1].n_orb;
+    if (tbme_len) for (int c = 0; c < 3; ++c) tbme_len[c] = h->layout.chan_len[c];
+    if (n_sd) { n_sd[0] = h->s[0].n_sd; n_sd[1] = h->s[1].n_sd; }
+    return CIH_OK;
+}
+
+int cih_basis_tables(cih_basis_h h, int32_t *orbitals, uint64_t *bits_p, uint64_t *bits_n,
+                     int32_t *nbeg, int32_t *ncnt, int64_t *rowbase)
+{
+    if (!h) return fail(CIH_ERR_ARG, "NULL handle");
+    if (orbitals) {
+        int k = 0;
+        for (int t = 0; t < 2; ++t)
+            for (int a = 0; a < h->s[t].n_orb; ++a, ++k) {
+                orbitals[4 * k] = h->s[t].oN[a];
+                orbitals[4 * k + 1] = h->s[t].ol[a];
+                orbitals[4 * k + 2] = h->s[t].oj2[a];
+                orbitals[4 * k + 3] = h->s[t].om2[a];
+            }
+    }
+    uint64_t *bits[2] = {bits_p, bits_n};
+    for (int t = 0; t < 2; ++t)
+        if (bits[t] && h->s[t].n_sd)
+            std::memcpy(bits[t], h->s[t].bits.data(), sizeof(uint64_t) * kMaxWords * h->s[t].n_sd);
+    if (nbeg && !h->nb.empty()) std::memcpy(nbeg, h->nb.data(), sizeof(int32_t) * h->nb.size());
+    if (ncnt && !h->nc.empty()) std::memcpy(ncnt, h->nc.data(), sizeof(int32_t) * h->nc.size());
+    if (rowbase) std::memcpy(rowbase, h->rowbase.data(), sizeof(int64_t) * h->rowbase.size());
+    return CIH_OK;
+}
+
+int cih_tbme_index(cih_basis_h h, int32_t a, int32_t b, int32_t c, int32_t d, int64_t *index, int32_t *sign)
+{
+    if (!h || !index || !sign) return fail(CIH_ERR_ARG, "NULL argument");
+    int ntot = h->s[0].n_orb + h->s[1].n_orb;
+    *index = -1;
+    *sign = 0;
+    if (a < 0 || b < 0 || c < 0 || d < 0 || a >= ntot || b >= ntot || c >= ntot || d >= ntot) return CIH_OK;
+    int32_t e1 = h->layout.pid[(size_t)a * ntot + b], e2 = h->layout.pid[(size_t)c * ntot + d];
+    if (e1 < 0 || e2 < 0 || ((e1 >> 16) & 0xFFF) != ((e2 >> 16) & 0xFFF)) return CIH_OK;
+    int g = (e1 >> 16) & 0xFFF;
+    int64_t u = e1 & 0xFFFF, v = e2 & 0xFFFF;
+    if (u > v) std::swap(u, v);
+    int64_t n = h->layout.gsize[g];
+    *index = h->layout.goff[g] + u * n - u * (u - 1) / 2 + (v - u);
+    *sign = (((e1 ^ e2) >> 30) & 1) ? -1 : 1;
+    return CIH_OK;
+}
+
+int cih_basis_destroy(cih_basis_h h)
+{
+    if (!h) return fail(CIH_ERR_ARG, "NULL handle");
+    release(h);
+    return CIH_OK;
+}
+
+static int needs_device(cih_basis_h h)
+{
+    if (!h) return fail(CIH_ERR_ARG, "NULL handle");
+    if (!h->dev_status) return fail(CIH_ERR_ARG, "host-only basis: build it with cih_basis_enumerate");
+    return CIH_OK;
+}
+
+int cih_ham_count(cih_basis_h h, int64_t *rowptr_dev, int64_t *nnz_out, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!rowptr_dev) return fail(CIH_ERR_ARG, "NULL rowptr");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = launch_count(*h, rowptr_dev, st))) return rc;
+    if ((rc = launch_scan(*h, rowptr_dev, st))) return rc;
+    if (nnz_out) {
+        cudaError_t e = cudaMemcpyAsync(nnz_out, rowptr_dev + h->dim, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "count: read nnz");
+    }
+    return CIH_OK;
+}
+
+int cih_ham_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,
+                 const float *tbme_dev, const double *e_sp_dev, int32_t *col_dev, float *val_dev, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!rowptr_dev || !col_dev || !val_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
+    if (!tbme_dev && h->layout.total > 0) return fail(CIH_ERR_ARG, "NULL two-body table");
+    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, e_sp_dev, col_dev, val_dev, (cudaStream_t)stream);
+}
+
+int cih_check(cih_basis_h h, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    int status = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&status, h->dev_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dev_status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "check");
+    if (status) return fail(CIH_ERR_DEVICE, "a kernel met a pair outside the two-body table layout");
+    return CIH_OK;
+}
+
+int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
+                       const float *val_dev, int32_t K, int32_t nev, int32_t max_iter, double tol,
+                       double *evals_host, double *evec0_dev, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!rowptr_dev || !col_dev || !val_dev || !evals_host) return fail(CIH_ERR_ARG, "NULL array");
+    if (K < 1 || nev < 1 || nev > 64 || max_iter < 1 || max_iter > 2048 || !(tol > 0))
+        return fail(CIH_ERR_ARG, "K, nev, max_iter or tol out of range");
+    return guarded([&]() -> int {
+        return lanczos(*h, rowptr_dev, col_dev, val_dev, K, nev, max_iter, tol, evals_host, evec0_dev,
+                       (cudaStream_t)stream);
+    });
+}
+
+int cih_ham_tbme_grad(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, const double *psi_dev,
+                      double *grad_dev, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!psi_dev || !grad_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
+    int64_t n = (int64_t)K * h->layout.total;
+    if (n == 0) return CIH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *acc = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&acc, sizeof(unsigned long long) * n, st);
+    if (e != cudaSuccess) return fail(CIH_ERR_NOMEM, std::string("gradient scratch: ") + cudaGetErrorString(e));
+    e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * n, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "gradient scratch clear");
+    if (!rc) rc = launch_grad(*h, rowptr_dev, K, psi_dev, acc, st);
+    if (!rc) rc = launch_grad_finish(n, acc, grad_dev, st);
+    cudaFreeAsync(acc, st);
+    return rc;
+}
+
+const char *cih_strerror(int code)
+{
+    switch (code) {
+    case CIH_OK: return "ok";
+    case CIH_ERR_ARG: return "invalid argument";
+    case CIH_ERR_NOMEM: return "out of memory";
+    case CIH_ERR_CAPACITY: return "result does not fit the capacity";
+    case CIH_ERR_TIMEOUT: return "bounded device wait timed out";
+    case CIH_ERR_UNSUPPORTED: return "size outside what the kernels handle";
+    case CIH_ERR_CUDA: return "CUDA runtime error";
+    case CIH_ERR_DEVICE: return "device-side check failed";
+    default: return "unknown error";
+    }
+}
+
+const char *cih_last_error_detail(void) { return g_detail.c_str(); }
+
+int cih_kernel_launches(int64_t *out)
+{
+    if (!out) return fail(CIH_ERR_ARG, "NULL argument");
+    *out = g_launches.load(std::memory_order_relaxed);
+    return CIH_OK;
+}
+
+}  // extern "C"

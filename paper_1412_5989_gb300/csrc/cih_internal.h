@@ -1,0 +1,139 @@
+// Internal data layout of libcih (host and device).  Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "cih.h"
+
+namespace cih {
+
+constexpr int kMaxWords = 4;              // <= 256 orbitals per species
+constexpr int kSortTile = 4096;           // longest neighbour list the sort handles
+
+// ---------------------------------------------------------------- device view
+
+// One species' sub-determinant tables and neighbour lists.
+struct DevSpecies {
+    const uint64_t *bits;      // n_sd x W words (W = basis word count)
+    const int8_t *N;           // oscillator quanta of each sub-det
+    const int32_t *cls_end;    // per sub-det: one past the end of its (2M, parity) class
+    const int64_t *fw_off;     // n_sd + 1: forward same-class neighbours (1 or 2 moves)
+    const int32_t *fw;         //   sorted ascending, all > x
+    const int64_t *n1_off;     // n_sd + 1: every one-move neighbour
+    const int32_t *n1;         //   sorted ascending
+    int32_t n_sd;
+    int32_t n_orb;
+    int32_t orb_base;          // combined index of this species' orbital 0
+};
+
+// Everything the Hamiltonian kernels read.
+struct DevBasis {
+    DevSpecies sp[2];          // 0 = protons, 1 = neutrons
+    const int32_t *nb;         // per proton sub-det: first neutron partner
+    const int32_t *nc;         //   number of partners
+    const int64_t *rowbase;    // n_p + 1: first row of each proton sub-det
+    const int8_t *orbN;        // combined orbital -> N
+    const int32_t *pid;        // ntot x ntot pair id (see pair_code), -1 = none
+    const int32_t *gsize;      // per global group: pairs in the group
+    const int64_t *goff;       // per global group: table offset of its triangle
+    int32_t n_p;
+    int32_t ntot;
+    int64_t dim;
+    int64_t tbme_len;
+};
+
+// pid entry: bits 0..15 local pair index u, bits 16..27 global group id,
+// bit 30 set when the orbitals are given in descending order (sign -1).
+__host__ __device__ inline int32_t pair_code(int group, int u, bool swapped)
+{
+    return (group << 16) | u | (swapped ? (1 << 30) : 0);
+}
+
+// ---------------------------------------------------------------- host side
+
+struct Species {
+    int Z = 0;
+    int n_orb = 0;
+    int N0 = 0, NF = -1;
+    int Nsub_max = 0;
+    std::vector<int> oN, ol, oj2, om2;       // orbital quantum numbers
+    int64_t n_sd = 0;
+    std::vector<uint64_t> bits;               // n_sd x kMaxWords
+    std::vector<int> N, M2;                   // per sub-det
+    std::vector<int> cls;                     // class id per sub-det
+    std::vector<int> cls_M2, cls_par, cls_begin, cls_end;
+};
+
+struct Layout {
+    // per channel (pp, nn, pn): pairs grouped, group metadata
+    int64_t chan_len[3] = {0, 0, 0};
+    int64_t total = 0;
+    std::vector<int32_t> gsize;               // global group id -> size
+    std::vector<int64_t> goff;                // global group id -> table offset
+    std::vector<int32_t> pid;                 // ntot x ntot
+};
+
+struct DevBuffers {
+    std::vector<void *> owned;                // every cudaMalloc made for the handle
+};
+
+}  // namespace cih
+
+struct cih_basis {
+    cih_space_t space{};
+    int W = 1;                                // words per bit string (1, 2 or 4)
+    int N0tot = 0, Nlim = 0;
+    cih::Species s[2];
+    int64_t dim = 0;
+    std::vector<int32_t> nb, nc;
+    std::vector<int64_t> rowbase;
+    cih::Layout layout;
+    cih::DevBasis dev{};
+    cih::DevBuffers buffers;
+    int64_t *scan_scratch = nullptr;          // block sums of the row-pointer scan
+    int64_t scan_scratch_len = 0;
+    int *dev_status = nullptr;                // kernel error word
+    int device = 0;
+};
+
+namespace cih {
+
+// every kernel launch site adds the launches it makes (capi.cpp)
+void count_launches(int64_t n);
+
+// error reporting (capi.cpp)
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+// host basis construction (basis.cpp)
+int build_host_basis(const cih_space_t &sp, cih_basis &b);
+
+// device set-up (neighbours.cu)
+int upload_and_build_neighbours(cih_basis &b, cudaStream_t st);
+
+// kernels (ham.cu)
+int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
+int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
+int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme,
+                const double *esp, int32_t *col, float *val, cudaStream_t st);
+int launch_grad(const cih_basis &b, const int64_t *rowptr, int K, const double *psi,
+                unsigned long long *acc, cudaStream_t st);
+int launch_grad_finish(int64_t n, const unsigned long long *acc, double *grad, cudaStream_t st);
+
+// generic device scans (scan.cu)
+int exclusive_scan_i64(int64_t *data, int64_t n, int64_t *block_sums, int64_t block_sums_len,
+                       cudaStream_t st);
+int64_t scan_scratch_needed(int64_t n);
+
+// symmetric tridiagonal eigenproblem, ascending, Z row-major n x n (tridiag.cpp)
+void tridiag_qr(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &Z);
+
+// Lanczos (lanczos.cu)
+int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val,
+            int K, int nev, int max_iter, double tol, double *evals, double *evec0, cudaStream_t st);
+
+}  // namespace cih
