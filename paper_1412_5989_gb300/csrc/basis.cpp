@@ -11,6 +11,8 @@
 // (2M, N mod 2, N, bits) order in linear time.
 #include <algorithm>
 #include <climits>
+#include <cstdint>
+#include <cstdlib>
 #include <map>
 #include <utility>
 
@@ -190,6 +192,51 @@ int build_layout(cih_basis &b)
     return CIH_OK;
 }
 
+// u(a, b) = S[a][kappa] + r(b) for every pn pair of the table (see PnSplit);
+// checked against the pair codes.
+int build_pn_split(cih_basis &b)
+{
+    const Species &P = b.s[0], &Q = b.s[1];
+    PnSplit &X = b.pn;
+    int ntot = P.n_orb + Q.n_orb;
+    // span covers every pn pair and every single orbital, so that the shifted
+    // 2m_a + span of a proton orbital is never negative
+    int span = 0;
+    for (int a = 0; a < P.n_orb; ++a) span = std::max(span, std::abs(P.om2[a]));
+    for (int c = 0; c < Q.n_orb; ++c) span = std::max(span, std::abs(Q.om2[c]));
+    for (int a = 0; a < P.n_orb; ++a)
+        for (int c = 0; c < Q.n_orb; ++c) span = std::max(span, std::abs(P.om2[a] + Q.om2[c]));
+    span += span & 1;                                  // keep 2m_a + 2m_b + span even
+    if (2 * span + 1 > 255) return fail(CIH_ERR_UNSUPPORTED, "orbital 2m range too wide for the packed moves");
+    X.m2span = span;
+    X.G = (span + 1) * 2;
+    X.S.assign((size_t)std::max(P.n_orb, 1) * X.G, 0);
+    X.gsize.assign(X.G, 0);
+    X.goff.assign(X.G, 0);
+    X.rn.assign(std::max(Q.n_orb, 1), 0);
+    for (int c = 0; c < Q.n_orb; ++c)
+        for (int e = 0; e < c; ++e)
+            if (Q.om2[e] == Q.om2[c] && ((Q.oN[e] ^ Q.oN[c]) & 1) == 0) X.rn[c]++;
+    if (b.layout.total > INT32_MAX) return fail(CIH_ERR_UNSUPPORTED, "two-body table above 2^31 entries");
+    std::vector<char> seen(X.S.size(), 0);
+    for (int a = 0; a < P.n_orb; ++a)
+        for (int c = 0; c < Q.n_orb; ++c) {
+            int32_t code = b.layout.pid[(size_t)a * ntot + P.n_orb + c];
+            if (code < 0) continue;
+            int g = (code >> 16) & 0xFFF, u = code & 0xFFFF;
+            int kappa = ((P.om2[a] + Q.om2[c] + span) / 2) * 2 + ((P.oN[a] + Q.oN[c]) & 1);
+            int s = u - X.rn[c];
+            size_t k = (size_t)a * X.G + kappa;
+            if (seen[k] && X.S[k] != s) return fail(CIH_ERR_UNSUPPORTED, "internal: pn pair split inconsistent");
+            if (s < INT16_MIN || s > INT16_MAX) return fail(CIH_ERR_UNSUPPORTED, "pn group too large");
+            seen[k] = 1;
+            X.S[k] = (int16_t)s;
+            X.gsize[kappa] = b.layout.gsize[g];
+            X.goff[kappa] = (int32_t)b.layout.goff[g];
+        }
+    return CIH_OK;
+}
+
 }  // namespace
 
 int build_host_basis(const cih_space_t &sp, cih_basis &b)
@@ -274,7 +321,9 @@ int build_host_basis(const cih_space_t &sp, cih_basis &b)
     b.rowbase[P.n_sd] = dim;
     b.dim = dim;
     if (dim > INT32_MAX) return fail(CIH_ERR_UNSUPPORTED, "dimension above 2^31-1 (int32 columns)");
-    return build_layout(b);
+    int rc = build_layout(b);
+    if (rc) return rc;
+    return build_pn_split(b);
 }
 
 }  // namespace cih

@@ -186,13 +186,19 @@ int cih_check(cih_basis_h h, void *stream)
 {
     int rc = needs_device(h);
     if (rc) return rc;
-    int status = 0;
+    int st4[4] = {0, 0, 0, 0};
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(&status, h->dev_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(st4, h->dev_status, sizeof(st4), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dev_status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dev_status + 2, 0, 2 * sizeof(int), st);
+    const int status = st4[0];
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "check");
-    if (status) return fail(CIH_ERR_DEVICE, "a kernel met a pair outside the two-body table layout");
+    if (status)
+        return fail(CIH_ERR_DEVICE, std::string("device status bits ") + std::to_string(status) +
+                                        " (1: pair outside the table layout, 2: write beyond the row, "
+                                        "4: two-move index, 8: deferred queue); first: " + std::to_string(st4[2]) + " " +
+                                        std::to_string(st4[3]));
     return CIH_OK;
 }
 

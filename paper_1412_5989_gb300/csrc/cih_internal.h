@@ -25,6 +25,7 @@ struct DevSpecies {
     const int32_t *fw;         //   sorted ascending, all > x
     const int64_t *n1_off;     // n_sd + 1: every one-move neighbour
     const int32_t *n1;         //   sorted ascending
+    const int64_t *n1_later;   // per sub-det: first one-move entry beyond its own class
     int32_t n_sd;
     int32_t n_orb;
     int32_t orb_base;          // combined index of this species' orbital 0
@@ -44,6 +45,29 @@ struct DevBasis {
     int32_t ntot;
     int64_t dim;
     int64_t tbme_len;
+    // fast paths
+    const int32_t *fw_tb[2];   // per forward entry: two-move table index << 1 | sign, or -1
+    const uint32_t *n1_info;   // per neutron one-move entry: packed move (see neighbours.cu)
+    const int16_t *pn_S;       // n_orb_p x pn_G
+    const int32_t *pn_gsize;   // pn_G
+    const int32_t *pn_goff;    // pn_G
+    const int8_t *m2p;         // proton orbital 2m
+    const int8_t *Np;          // proton orbital N
+    int32_t pn_G;
+    int32_t pn_m2span;
+    int32_t max_cand;          // largest candidate list of a proton sub-det
+    int *queue;                // work counter (unused by the row kernels)
+    // candidate table: for proton sub-det p, entries cand_off[p] .. cand_off[p+1]
+    // (later same-class sub-dets with one or two protons moved, then later-class
+    // sub-dets with one proton moved, ascending), structure of arrays:
+    const int64_t *cand_off;
+    const int32_t *cand_colbase;   // rowbase[q] - nbeg[q]
+    const int32_t *cand_lo;        // nbeg[q]
+    const int32_t *cand_hi;        // nbeg[q] + ncnt[q], two-move flag in bit 30
+    const uint32_t *cand_uv;       // one-move: S row bases A_u | A_v << 16; two-move: table index << 1 | sign
+    const uint32_t *cand_mv;       // one-move: K_a | N_a << 8 | sign << 9 | a << 16 | c << 24
+    const int32_t *row_p;          // row -> proton sub-det
+    int32_t A;                     // particles
 };
 
 // pid entry: bits 0..15 local pair index u, bits 16..27 global group id,
@@ -52,6 +76,20 @@ __host__ __device__ inline int32_t pair_code(int group, int u, bool swapped)
 {
     return (group << 16) | u | (swapped ? (1 << 30) : 0);
 }
+
+// device tables of one species used while building the neighbour lists
+struct SpeciesBuild {
+    const uint64_t *bits;      // n_sd x W
+    const int8_t *N;
+    const int16_t *M2;
+    const int32_t *cls_end;
+    const int32_t *cls_lookup;  // (M2 + moff) * 2 + parity -> class id, -1 if none
+    const int32_t *cls_begin;
+    const int32_t *cls_endc;    // per class
+    const int8_t *oN;           // per orbital
+    const int16_t *om2;
+    int32_t n_sd, n_orb, moff, mspan, Nsub_max;
+};
 
 // ---------------------------------------------------------------- host side
 
@@ -77,6 +115,18 @@ struct Layout {
     std::vector<int32_t> pid;                 // ntot x ntot
 };
 
+// pn pair index split u(a, b) = S[a][kappa] + r(b): kappa = dense group key
+// ((2m_a + 2m_b + m2span) / 2) * 2 + ((N_a + N_b) & 1), r(b) = number of lower
+// neutron orbitals with the same 2m and N parity as b.  Groups absent from the
+// table have size 0.
+struct PnSplit {
+    int G = 0;                                // dense group keys
+    int m2span = 0;                           // largest |2m_a + 2m_b|
+    std::vector<int16_t> S;                   // n_orb_p x G
+    std::vector<int32_t> gsize, goff;         // per dense key
+    std::vector<int32_t> rn;                  // per neutron orbital
+};
+
 struct DevBuffers {
     std::vector<void *> owned;                // every cudaMalloc made for the handle
 };
@@ -92,6 +142,8 @@ struct cih_basis {
     std::vector<int32_t> nb, nc;
     std::vector<int64_t> rowbase;
     cih::Layout layout;
+    cih::PnSplit pn;
+    cih::SpeciesBuild sbuild[2]{};
     cih::DevBasis dev{};
     cih::DevBuffers buffers;
     int64_t *scan_scratch = nullptr;          // block sums of the row-pointer scan

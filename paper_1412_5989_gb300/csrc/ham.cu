@@ -317,162 +317,439 @@ __device__ __forceinline__ int64_t lower_bound(const int32_t *list, int64_t lo, 
     return lo;
 }
 
-template <int W, int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_walk(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs G, int *status)
+// ---------------------------------------------------------------- row kernel
+//
+// Warps walk rows independently (grid-stride); a CTA only shares the pn
+// split table S in shared memory.  For row (p, n):
+//   diagonal  - the warp sums the one-body energies and every occupied pair
+//               (lanes over pairs, FP64 reduction);
+//   A         - n's forward same-class neighbours inside p's partner range:
+//               two-moves from their precomputed table index, one-moves
+//               deferred;
+//   B         - p's candidate table in chunks of 32: lane k finds its
+//               segment (n itself if inside q's range, plus n's one-move
+//               neighbours inside it, by binary search), a warp scan places
+//               the segments and the chunk's elements are emitted flattened
+//               (lane e writes element e: contiguous stores).  pp two-moves use
+//               the precomputed index, pn elements u(a,b) = S[a][kappa] + r(b),
+//               proton one-moves are deferred;
+//   deferred  - one-move elements, lanes over (element, spectator) pairs and
+//               a segmented FP64 reduction.
+
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr int kGroupCap = 128;
+constexpr int kSlowCap = 64;
+constexpr int kMaxA = 64;
+constexpr int kPairCap = kMaxA * (kMaxA - 1) / 2;
+
+namespace sm {
+constexpr int gsize = 0;                                   // int32[kGroupCap]
+constexpr int goff = gsize + kGroupCap * 4;                // int32[kGroupCap]
+constexpr int pi = goff + kGroupCap * 4;                   // uint8[kPairCap]
+constexpr int pj = pi + kPairCap;                          // uint8[kPairCap]
+constexpr int warp0 = (pj + kPairCap + 15) / 16 * 16;
+// per warp
+constexpr int w_incl = 0;                                  // int32[32]
+constexpr int w_n1 = w_incl + 128;                         // int32[32]
+constexpr int w_ins = w_n1 + 128;                          // int32[32]
+constexpr int w_cb = w_ins + 128;                          // int32[32]
+constexpr int w_uv = w_cb + 128;                           // uint32[32]
+constexpr int w_mv = w_uv + 128;                           // uint32[32]
+constexpr int w_hi = w_mv + 128;                           // int32[32]
+constexpr int w_spos = w_hi + 128;                         // int32[kSlowCap]
+constexpr int w_scol = w_spos + kSlowCap * 4;              // int32[kSlowCap]
+constexpr int w_scode = w_scol + kSlowCap * 4;             // uint32[kSlowCap]
+constexpr int w_occ = w_scode + kSlowCap * 4;              // int16[kMaxA]
+constexpr int w_size = w_occ + kMaxA * 2;
+constexpr int S = warp0 + kWarps * w_size;                 // int16[n_orb_p * G]
+}  // namespace sm
+
+__host__ __device__ inline size_t smem_bytes(int nS) { return (size_t)sm::S + ((size_t)nS * 2 + 15) / 16 * 16; }
+
+template <class T>
+__device__ __forceinline__ T *sptr(unsigned char *base, int off) { return reinterpret_cast<T *>(base + off); }
+
+__device__ __forceinline__ double warp_sum(double v, int width)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const DevSpecies &SP = B.sp[0], &SN = B.sp[1];
-    const int nbase = SN.orb_base;
-    const unsigned lt = (1u << lane) - 1;
+    for (int d = width >> 1; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d, width);
+    return v;
+}
 
-    if (MODE == 1) F.nnz = rowptr[B.dim];       // set stride of the values
-    for (int64_t row = gw; row < B.dim; row += nw) {
-        // proton sub-det of the row: last p with rowbase[p] <= row
-        int lo = 0, hi = B.n_p - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (B.rowbase[mid] <= row) lo = mid; else hi = mid - 1;
-        }
-        const int p = lo;
-        const int nbp = B.nb[p];
-        const int n = nbp + (int)(row - B.rowbase[p]);
-        const int nend = nbp + B.nc[p];
-        uint64_t pb[W], nbits[W];
-        ld_bits<W>(SP.bits, p, pb);
-        ld_bits<W>(SN.bits, n, nbits);
-        const int64_t out = MODE == 1 ? rowptr[row] : 0;
-        const int64_t lim = MODE == 1 ? min(rowptr[row + 1], F.nnz) : 0;
-        int64_t pos = 0;
-        double diag1 = 0.0;
-        if (MODE == 1) diag1 = one_body<W>(B, F, pb, nbits);
+// table index of a pn element from the candidate (uv, mv) and neutron move (ni)
+__device__ __forceinline__ int64_t pn_index(const unsigned char *sb, uint32_t uv, uint32_t mv, uint32_t ni, int &sign)
+{
+    const int16_t *S = reinterpret_cast<const int16_t *>(sb + sm::S);
+    const int32_t *gs = reinterpret_cast<const int32_t *>(sb + sm::gsize);
+    const int32_t *go = reinterpret_cast<const int32_t *>(sb + sm::goff);
+    const int t = (int)((ni >> 16) & 0x7F) - 64 + (int)(((mv >> 8) ^ (ni >> 23)) & 1);
+    const int kappa = (int)(mv & 0xFF) + t;
+    int u = S[(int)(uv & 0xFFFF) + t] + (int)((ni >> 8) & 0xFF);
+    int v = S[(int)(uv >> 16) + t] + (int)(ni & 0xFF);
+    if (u > v) { const int x = u; u = v; v = x; }
+    const int64_t n = gs[kappa];
+    sign = (int)(((mv >> 9) ^ (ni >> 24)) & 1);
+    return (int64_t)go[kappa] + (int64_t)u * n - (int64_t)u * (u - 1) / 2 + (v - u);
+}
 
-        // ---- A: diagonal, then same-class forward neutron neighbours in p's range
-        if (lane == 0 && MODE != 0) {
-            Elem<W> e;
-            make_diag<W>(e, pb, nbits);
-            emit<W, MODE>(B, F, G, status, out, lim, row, row, e, diag1);
+// one single-term element (table index, sign bit) at position o
+template <int MODE>
+__device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F, const GradArgs &Gr, int *status,
+                                           int64_t o, int64_t lim, int64_t nnz, int64_t row, int64_t colj,
+                                           int64_t idx, int sgn)
+{
+    if (MODE == 1) {
+        if (o >= lim) { atomicOr(status, 2); return; }
+        F.col[o] = (int32_t)colj;
+        for (int k = 0; k < F.K; ++k) {
+            const float v = __ldg(F.tbme + (int64_t)k * B.tbme_len + idx);
+            F.val[(int64_t)k * nnz + o] = sgn ? -v : v;
         }
-        pos = 1;
-        {
-            const int64_t f0 = SN.fw_off[n], f1 = SN.fw_off[n + 1];
-            for (int64_t t0 = f0; t0 < f1; t0 += 32) {
-                int64_t t = t0 + lane;
-                int y = t < f1 ? SN.fw[t] : INT32_MAX;
-                bool in = y < nend;
-                unsigned m = __ballot_sync(0xffffffffu, in);
-                if (MODE != 0 && in) {
-                    uint64_t yb[W];
-                    ld_bits<W>(SN.bits, y, yb);
-                    Elem<W> e;
-                    if (popc_xor<W>(nbits, yb) == 2) make_one<W>(e, 1, nbase, nbits, yb, pb);
-                    else make_two<W>(e, 1, nbase, nbits, yb);
-                    emit<W, MODE>(B, F, G, status, out + pos + __popc(m & lt), lim, row,
-                                  B.rowbase[p] + (y - nbp), e, diag1);
-                }
-                pos += __popc(m);
-                if (m != 0xffffffffu) break;          // sorted: nothing later is < nend
-            }
+    } else if (MODE == 2) {
+        for (int k = 0; k < Gr.K; ++k) {
+            const double *psi = Gr.psi + (int64_t)k * B.dim;
+            const double f = 2.0 * psi[row] * psi[colj];
+            const long long qv = __double2ll_rn((sgn ? -f : f) * kFixScale);
+            atomicAdd(Gr.acc + (int64_t)k * B.tbme_len + idx, (unsigned long long)qv);
         }
-
-        // ---- B: later proton sub-dets
-        const int64_t n1a = SN.n1_off[n], n1b = SN.n1_off[n + 1];
-        const int64_t self_ins = lower_bound(SN.n1, n1a, n1b, n);   // where n sorts among its neighbours
-        for (int list = 0; list < 2; ++list) {
-            int64_t c0, c1;
-            if (list == 0) {
-                c0 = SP.fw_off[p]; c1 = SP.fw_off[p + 1];
-            } else {
-                c1 = SP.n1_off[p + 1];
-                c0 = lower_bound(SP.n1, SP.n1_off[p], c1, SP.cls_end[p]);
-            }
-            const int32_t *cand = list == 0 ? SP.fw : SP.n1;
-            for (int64_t k0 = c0; k0 < c1; k0 += 32) {
-                int64_t k = k0 + lane;
-                int q = -1, dp = 0;
-                int64_t lo1 = 0, hi1 = 0;
-                bool self = false;
-                int len = 0;
-                uint64_t qb[W];
-                if (k < c1) {
-                    q = cand[k];
-                    ld_bits<W>(SP.bits, q, qb);
-                    dp = popc_xor<W>(pb, qb) >> 1;
-                    const int qb0 = B.nb[q], qb1 = qb0 + B.nc[q];
-                    self = n >= qb0 && n < qb1;
-                    if (dp == 2) {
-                        len = self ? 1 : 0;
-                    } else {
-                        lo1 = lower_bound(SN.n1, n1a, n1b, qb0);
-                        hi1 = lower_bound(SN.n1, lo1, n1b, qb1);
-                        len = (int)(hi1 - lo1) + (self ? 1 : 0);
-                    }
-                }
-                // warp exclusive scan of len
-                int inc = len;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    int o = __shfl_up_sync(0xffffffffu, inc, d);
-                    if (lane >= d) inc += o;
-                }
-                const int tot = __shfl_sync(0xffffffffu, inc, 31);
-                if (MODE != 0 && len > 0) {
-                    int64_t o = out + pos + (inc - len);
-                    const int64_t cbase = B.rowbase[q] - B.nb[q];
-                    if (dp == 2) {
-                        Elem<W> e;
-                        make_two<W>(e, 0, 0, pb, qb);
-                        emit<W, MODE>(B, F, G, status, o, lim, row, cbase + n, e, diag1);
-                    } else {
-                        const int64_t ins = self ? (min(max(self_ins, lo1), hi1) - lo1) : -1;
-                        for (int t = 0; t < len; ++t) {
-                            Elem<W> e;
-                            int nj;
-                            if (t == ins) {
-                                nj = n;
-                                make_one<W>(e, 0, 0, pb, qb, nbits);
-                            } else {
-                                nj = SN.n1[lo1 + t - ((ins >= 0 && t > ins) ? 1 : 0)];
-                                uint64_t yb[W];
-                                ld_bits<W>(SN.bits, nj, yb);
-                                make_pn<W>(e, nbase, pb, qb, nbits, yb);
-                            }
-                            emit<W, MODE>(B, F, G, status, o + t, lim, row, cbase + nj, e, diag1);
-                        }
-                    }
-                }
-                pos += tot;
-            }
-        }
-        if (MODE == 0 && lane == 0) counts[row] = pos;
     }
 }
 
-int grid_rows(int64_t rows)
+template <int W>
+__device__ __forceinline__ int nth_bit(const uint64_t (&x)[W], int i)
 {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (rows + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 32));
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int c = __popcll(x[w]);
+        if (i < c) {
+            uint64_t m = x[w];
+            for (int k = 0; k < i; ++k) m &= m - 1;
+            return w * 64 + __ffsll((long long)m) - 1;
+        }
+        i -= c;
+    }
+    return -1;
+}
+
+// Deferred one-move elements of a row: lanes over (element, spectator)
+// pairs, groups of the next power of two >= A-1 lanes, FP64 segmented sum.
+// The queue holds row-relative positions, columns and packed moves
+// (bra-only a, ket-only c, sign, neutron flag in bit 31).
+template <int MODE>
+__device__ __noinline__ void flush_slow(const DevBasis &B, const FillArgs &F, const GradArgs &Gr, int *status,
+                                        const int16_t *w_occ, const int32_t *w_spos, const int32_t *w_scol,
+                                        const uint32_t *w_scode, int &nslow, int64_t out, int64_t lim, int64_t nnz,
+                                        int64_t row)
+{
+    const int lane = threadIdx.x & 31;
+    const int A = B.A, nbase = B.sp[1].orb_base;
+    __syncwarp();
+    const int ns = nslow;
+    const int sp_n = A - 1;
+    int gsz = 1;
+    while (gsz < sp_n) gsz <<= 1;
+    const int per = 32 / gsz;
+    for (int e0 = 0; e0 < ns; e0 += per) {
+        const int e = e0 + lane / gsz;
+        const int i = lane % gsz;
+        const bool act = e < ns;
+        const uint32_t code = act ? w_scode[e] : 0;
+        const int base = (code >> 31) ? nbase : 0;
+        const int a = base + (int)(code & 0xFF), c = base + (int)((code >> 8) & 0xFF);
+        const int sgn = (code >> 16) & 1;
+        int ia = 0;
+        for (int x = 0; x < A; ++x) ia += (w_occ[x] < a);
+        const bool has = act && i < sp_n;
+        const int kspec = has ? w_occ[i + (i >= ia ? 1 : 0)] : 0;
+        const int64_t o = out + (act ? w_spos[e] : 0);
+        const int64_t colj = act ? w_scol[e] : 0;
+        int64_t idx = 0;
+        int sg = 1;
+        bool ok = true;
+        if (has) ok = tbme_at(B, a, kspec, c, kspec, idx, sg);
+        if (!ok && atomicOr(status, 1) == 0) {
+            status[2] = a | (kspec << 8) | (c << 16) | (kspec << 24);
+            status[3] = 2 | (ns << 8) | (ia << 16) | (A << 24);
+        }
+        for (int kk = 0; kk < (MODE == 1 ? F.K : Gr.K); ++kk) {
+            if (MODE == 1) {
+                double v = 0.0;
+                if (has && ok) v = sg * (double)__ldg(F.tbme + (int64_t)kk * B.tbme_len + idx);
+                v = warp_sum(v, gsz);
+                if (act && i == 0) {
+                    if (o < lim) {
+                        if (kk == 0) F.col[o] = (int32_t)colj;
+                        F.val[(int64_t)kk * nnz + o] = (float)(sgn ? -v : v);
+                    } else {
+                        atomicOr(status, 2);
+                    }
+                }
+            } else if (has && ok) {
+                const double f = 2.0 * Gr.psi[(int64_t)kk * B.dim + row] * Gr.psi[(int64_t)kk * B.dim + colj];
+                const long long qv = __double2ll_rn((sgn ? -1 : 1) * sg * f * kFixScale);
+                atomicAdd(Gr.acc + (int64_t)kk * B.tbme_len + idx, (unsigned long long)qv);
+            }
+        }
+    }
+    __syncwarp();
+    nslow = 0;
+}
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(kThreads, 2)
+k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs Gr, int *status)
+{
+    extern __shared__ __align__(16) unsigned char sb[];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned lt = (1u << lane) - 1;
+    const DevSpecies &SP = B.sp[0], &SN = B.sp[1];
+    const int A = B.A, nbase = SN.orb_base;
+    const int npairs = A * (A - 1) / 2;
+    if (MODE != 0) {
+        const int G = B.pn_G, nS = SP.n_orb * G;
+        int16_t *S = sptr<int16_t>(sb, sm::S);
+        int32_t *gs = sptr<int32_t>(sb, sm::gsize), *go = sptr<int32_t>(sb, sm::goff);
+        for (int i = tid; i < nS; i += kThreads) S[i] = B.pn_S[i];
+        for (int i = tid; i < G; i += kThreads) { gs[i] = B.pn_gsize[i]; go[i] = B.pn_goff[i]; }
+        uint8_t *pi = sptr<uint8_t>(sb, sm::pi), *pj = sptr<uint8_t>(sb, sm::pj);
+        for (int l = tid; l < npairs; l += kThreads) {     // pair l -> (i, j), i < j
+            int i = 0, r = l;
+            while (r >= A - 1 - i) { r -= A - 1 - i; ++i; }
+            pi[l] = (uint8_t)i;
+            pj[l] = (uint8_t)(i + 1 + r);
+        }
+        __syncthreads();
+    }
+    const int64_t nnz = MODE == 1 ? rowptr[B.dim] : 0;
+    unsigned char *wb = sb + sm::warp0 + wid * sm::w_size;
+    int32_t *w_incl = sptr<int32_t>(wb, sm::w_incl), *w_n1 = sptr<int32_t>(wb, sm::w_n1);
+    int32_t *w_ins = sptr<int32_t>(wb, sm::w_ins), *w_cb = sptr<int32_t>(wb, sm::w_cb);
+    uint32_t *w_uv = sptr<uint32_t>(wb, sm::w_uv), *w_mv = sptr<uint32_t>(wb, sm::w_mv);
+    int32_t *w_hi = sptr<int32_t>(wb, sm::w_hi);
+    int32_t *w_spos = sptr<int32_t>(wb, sm::w_spos), *w_scol = sptr<int32_t>(wb, sm::w_scol);
+    uint32_t *w_scode = sptr<uint32_t>(wb, sm::w_scode);
+    int16_t *w_occ = sptr<int16_t>(wb, sm::w_occ);
+    const int64_t gw = (blockIdx.x * (int64_t)kThreads + tid) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+
+    for (int64_t row = gw; row < B.dim; row += nw) {
+        const int p = B.row_p[row];
+        const int nbp = B.nb[p];
+        const int64_t rbp = B.rowbase[p];
+        const int n = nbp + (int)(row - rbp);
+        const int nend = nbp + B.nc[p];
+        const int64_t cbp = rbp - nbp;
+        const int64_t out = MODE == 1 ? rowptr[row] : 0;
+        const int64_t lim = MODE == 1 ? min(rowptr[row + 1], nnz) : 0;
+        int nslow = 0;
+
+        // ---- diagonal: occupied orbitals (combined, ascending), then all pairs
+        if (MODE != 0) {
+            uint64_t pb[W], nbits[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) { pb[w] = SP.bits[(int64_t)p * W + w]; nbits[w] = SN.bits[(int64_t)n * W + w]; }
+            int zp = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) zp += __popcll(pb[w]);
+            for (int i = lane; i < A; i += 32)
+                w_occ[i] = (int16_t)(i < zp ? nth_bit<W>(pb, i) : nbase + nth_bit<W>(nbits, i - zp));
+            __syncwarp();
+            const uint8_t *pi = sptr<uint8_t>(sb, sm::pi), *pj = sptr<uint8_t>(sb, sm::pj);
+            for (int k = 0; k < (MODE == 1 ? F.K : Gr.K); ++k) {
+                double acc = 0.0;
+                for (int l = lane; l < npairs; l += 32) {
+                    const int a = w_occ[pi[l]], c = w_occ[pj[l]];
+                    int64_t idx;
+                    int sg;
+                    if (!tbme_at(B, a, c, a, c, idx, sg)) {
+                        if (atomicOr(status, 1) == 0) { status[2] = a | (c << 8) | (a << 16) | (c << 24); status[3] = 1; }
+                        continue;
+                    }
+                    if (MODE == 1) {
+                        acc += sg * (double)__ldg(F.tbme + (int64_t)k * B.tbme_len + idx);
+                    } else {
+                        const double pr = Gr.psi[(int64_t)k * B.dim + row];
+                        const long long qv = __double2ll_rn(sg * pr * pr * kFixScale);
+                        atomicAdd(Gr.acc + (int64_t)k * B.tbme_len + idx, (unsigned long long)qv);
+                    }
+                }
+                if (MODE == 1) {
+                    for (int i = lane; i < A; i += 32) {
+                        const int a = w_occ[i];
+                        acc += F.esp ? F.esp[a] : F.hw * ((double)B.orbN[a] + 1.5);
+                    }
+                    acc = warp_sum(acc, 32);
+                    if (lane == 0) {
+                        if (out < lim) {
+                            if (k == 0) F.col[out] = (int32_t)row;
+                            F.val[(int64_t)k * nnz + out] = (float)acc;
+                        } else {
+                            atomicOr(status, 2);
+                        }
+                    }
+                }
+            }
+        }
+        int64_t pos = 1;
+
+        // ---- A: same-class forward neutron neighbours inside p's range
+        {
+            const int64_t a0 = SN.fw_off[n], a1 = SN.fw_off[n + 1];
+            for (int64_t t0 = a0; t0 < a1; t0 += 32) {
+                const int64_t t = t0 + lane;
+                const int y = t < a1 ? SN.fw[t] : INT32_MAX;
+                const bool in = y < nend;
+                const unsigned bm = __ballot_sync(0xffffffffu, in);
+                if (MODE != 0) {
+                    if (nslow > kSlowCap - 32)
+                        flush_slow<MODE>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, out, lim, nnz, row);
+                    const int32_t tb = in ? B.fw_tb[1][t] : 0;
+                    const bool slow = in && tb < 0;
+                    const unsigned sm_ = __ballot_sync(0xffffffffu, slow);
+                    if (in && !slow)
+                        put_single<MODE>(B, F, Gr, status, out + pos + __popc(bm & lt), lim, nnz, row, cbp + y,
+                                         tb >> 1, tb & 1);
+                    if (slow) {
+                        const int q = nslow + __popc(sm_ & lt);
+                        if (q < kSlowCap) {
+                            w_spos[q] = (int32_t)(pos + __popc(bm & lt));
+                            w_scol[q] = (int32_t)(cbp + y);
+                            w_scode[q] = (uint32_t)~tb | (1u << 31);        // neutron one-move
+                        } else {
+                            atomicOr(status, 8);
+                        }
+                    }
+                    nslow += __popc(sm_);
+                }
+                pos += __popc(bm);
+                if (bm != 0xffffffffu) break;
+            }
+        }
+
+        // ---- B: candidates of p in chunks of 32
+        const int64_t c0 = B.cand_off[p], c1 = B.cand_off[p + 1];
+        const int64_t n1a = SN.n1_off[n], n1b = SN.n1_off[n + 1];
+        const int64_t self_ins = lower_bound(SN.n1, n1a, n1b, n);
+        for (int64_t k0 = c0; k0 < c1; k0 += 32) {
+            const int64_t k = k0 + lane;
+            int len = 0, ins = -1, hi = 0;
+            int64_t s1 = n1a;
+            if (k < c1) {
+                const int lo = B.cand_lo[k];
+                hi = B.cand_hi[k];
+                const int hr = hi & 0x3FFFFFFF;
+                const bool self = n >= lo && n < hr;
+                if (hi >> 30) {
+                    len = self;
+                } else {
+                    s1 = lower_bound(SN.n1, n1a, n1b, lo);
+                    const int64_t e1 = lower_bound(SN.n1, s1, n1b, hr);
+                    len = (int)(e1 - s1) + (self ? 1 : 0);
+                    if (self) ins = (int)(min(max(self_ins, s1), e1) - s1);
+                }
+            }
+            int incl = len;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int o2 = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += o2;
+            }
+            const int T = __shfl_sync(0xffffffffu, incl, 31);
+            if (MODE != 0 && T > 0) {
+                w_incl[lane] = incl;
+                w_n1[lane] = (int32_t)(s1 - n1a);
+                w_ins[lane] = ins;
+                w_hi[lane] = hi;
+                if (k < c1) {
+                    w_cb[lane] = B.cand_colbase[k];
+                    w_uv[lane] = B.cand_uv[k];
+                    w_mv[lane] = B.cand_mv[k];
+                }
+                __syncwarp();
+                const int iters = (T + 31) >> 5;                   // same for every lane
+                for (int it = 0; it < iters; ++it) {
+                    if (nslow > kSlowCap - 32)
+                        flush_slow<MODE>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, out, lim, nnz, row);
+                    const int e = (it << 5) + lane;
+                    const bool act = e < T;
+                    int j = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (w_incl[j + step - 1] <= e) j += step;
+                    bool slow = false;
+                    int64_t colj = 0;
+                    if (act) {
+                        const int tt = e - (j ? w_incl[j - 1] : 0);
+                        const int64_t o = out + pos + e;
+                        const int64_t cb = w_cb[j];
+                        const uint32_t uv = w_uv[j];
+                        if (w_hi[j] >> 30) {
+                            put_single<MODE>(B, F, Gr, status, o, lim, nnz, row, cb + n, (int64_t)(uv >> 1), uv & 1);
+                        } else {
+                            const int insj = w_ins[j];
+                            if (tt == insj) {
+                                slow = true;
+                                colj = cb + n;
+                            } else {
+                                const int64_t np = n1a + w_n1[j] + tt - ((insj >= 0 && tt > insj) ? 1 : 0);
+                                int sg;
+                                const int64_t idx = pn_index(sb, uv, w_mv[j], B.n1_info[np], sg);
+                                put_single<MODE>(B, F, Gr, status, o, lim, nnz, row, cb + SN.n1[np], idx, sg);
+                            }
+                        }
+                    }
+                    const unsigned sm_ = __ballot_sync(0xffffffffu, slow);
+                    if (slow) {
+                        const int q = nslow + __popc(sm_ & lt);
+                        if (q < kSlowCap) {
+                            const uint32_t mv = w_mv[j];
+                            w_spos[q] = (int32_t)(pos + e);
+                            w_scol[q] = (int32_t)colj;
+                            w_scode[q] = ((mv >> 16) & 0xFF) | (((mv >> 24) & 0xFF) << 8) | (((mv >> 9) & 1) << 16);
+                        } else {
+                            atomicOr(status, 8);
+                        }
+                    }
+                    nslow += __popc(sm_);
+                }
+                __syncwarp();
+            }
+            pos += T;
+        }
+
+        if (MODE != 0 && nslow > 0) flush_slow<MODE>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, out, lim, nnz, row);
+        if (MODE == 0 && lane == 0) counts[row] = pos;
+        __syncwarp();
+    }
 }
 
 template <int MODE>
-int launch_walk(const cih_basis &b, const int64_t *rowptr, int64_t *counts, const FillArgs &F,
-                const GradArgs &G, cudaStream_t st)
+int launch_rows(const cih_basis &b, const int64_t *rowptr, int64_t *counts, const FillArgs &F, const GradArgs &G,
+                cudaStream_t st)
 {
     if (b.dim == 0) return CIH_OK;
-    int grid = grid_rows(b.dim);
-    dim3 blk(kWarpsPerBlock * 32);
-    count_launches(1);
-    if (b.W == 1) k_walk<1, MODE><<<grid, blk, 0, st>>>(b.dev, rowptr, counts, F, G, b.dev_status);
-    else if (b.W == 2) k_walk<2, MODE><<<grid, blk, 0, st>>>(b.dev, rowptr, counts, F, G, b.dev_status);
-    else k_walk<4, MODE><<<grid, blk, 0, st>>>(b.dev, rowptr, counts, F, G, b.dev_status);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "row walk launch");
-    return CIH_OK;
+    const DevBasis &D = b.dev;
+    if (D.pn_G > kGroupCap || D.A > kMaxA || D.A - 1 > 32)
+        return fail(CIH_ERR_UNSUPPORTED, "more than 33 particles or pn groups above the row kernel's capacity");
+    const size_t smem = MODE == 0 ? (size_t)sm::S : smem_bytes(D.sp[0].n_orb * D.pn_G);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto go = [&](auto kern) -> int {
+        cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (ee != cudaSuccess) return cuda_fail(ee, "row kernel shared memory");
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+        const int64_t want = (b.dim + kWarps - 1) / kWarps;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), want));
+        count_launches(1);
+        kern<<<grid, kThreads, smem, st>>>(D, rowptr, counts, F, G, b.dev_status);
+        ee = cudaGetLastError();
+        return ee == cudaSuccess ? CIH_OK : cuda_fail(ee, "row kernel launch");
+    };
+    if (b.W == 1) return go(k_rows<1, MODE>);
+    if (b.W == 2) return go(k_rows<2, MODE>);
+    return go(k_rows<4, MODE>);
 }
 
 __global__ void k_fix_to_double(int64_t n, const unsigned long long *acc, double *out)
@@ -485,7 +762,7 @@ __global__ void k_fix_to_double(int64_t n, const unsigned long long *acc, double
 
 int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st)
 {
-    return launch_walk<0>(b, nullptr, rowptr, FillArgs{}, GradArgs{}, st);
+    return launch_rows<0>(b, nullptr, rowptr, FillArgs{}, GradArgs{}, st);
 }
 
 int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st)
@@ -497,14 +774,14 @@ int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, con
                 const double *esp, int32_t *col, float *val, cudaStream_t st)
 {
     FillArgs F{K, hw, tbme, esp, col, val, 0};
-    return launch_walk<1>(b, rowptr, nullptr, F, GradArgs{}, st);
+    return launch_rows<1>(b, rowptr, nullptr, F, GradArgs{}, st);
 }
 
 int launch_grad(const cih_basis &b, const int64_t *rowptr, int K, const double *psi,
                 unsigned long long *acc, cudaStream_t st)
 {
     GradArgs G{K, psi, acc};
-    return launch_walk<2>(b, rowptr, nullptr, FillArgs{}, G, st);
+    return launch_rows<2>(b, rowptr, nullptr, FillArgs{}, G, st);
 }
 
 int launch_grad_finish(int64_t n, const unsigned long long *acc, double *grad, cudaStream_t st)

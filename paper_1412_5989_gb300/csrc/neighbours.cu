@@ -17,18 +17,7 @@
 namespace cih {
 namespace {
 
-struct SpeciesBuild {
-    const uint64_t *bits;      // n_sd x W
-    const int8_t *N;
-    const int16_t *M2;
-    const int32_t *cls_end;
-    const int32_t *cls_lookup;  // (M2 + moff) * 2 + parity -> class id, -1 if none
-    const int32_t *cls_begin;
-    const int32_t *cls_endc;    // per class
-    const int8_t *oN;           // per orbital
-    const int16_t *om2;
-    int32_t n_sd, n_orb, moff, mspan, Nsub_max;
-};
+
 
 template <int W>
 __device__ __forceinline__ void load_bits(const uint64_t *base, int64_t i, uint64_t (&o)[W])
@@ -181,6 +170,182 @@ __global__ void k_sort_lists(const int64_t *off, int32_t *data, int64_t n)
     }
 }
 
+template <int W>
+__device__ __forceinline__ int low_bit(const uint64_t (&x)[W])
+{
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        if (x[w]) return w * 64 + __ffsll((long long)x[w]) - 1;
+    return -1;
+}
+
+template <int W>
+__device__ __forceinline__ int count_below(const uint64_t (&R)[W], int k)
+{
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        int lo = w * 64;
+        if (k >= lo + 64) c += __popcll(R[w]);
+        else if (k > lo) c += __popcll(R[w] & ((1ull << (k - lo)) - 1));
+    }
+    return c;
+}
+
+// Packed one-move of each neutron list entry, bra x -> ket y:
+//   b = orbital in x only, d = orbital in y only, R = common orbitals;
+//   bits 0..7 r(d), 8..15 r(b), 16..22 2m_b + 64, 23 N_b & 1,
+//   24 sign (-1)^(#R below b + #R below d).
+template <int W>
+__global__ void k_n1_info(SpeciesBuild S, const int64_t *off, const int32_t *list, const int32_t *rn,
+                          uint32_t *info)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp; x < S.n_sd; x += nwarps) {
+        uint64_t bx[W];
+        load_bits<W>(S.bits, x, bx);
+        for (int64_t t = off[x] + lane; t < off[x + 1]; t += 32) {
+            uint64_t by[W], R[W], dx[W], dy[W];
+            load_bits<W>(S.bits, list[t], by);
+#pragma unroll
+            for (int w = 0; w < W; ++w) { R[w] = bx[w] & by[w]; dx[w] = bx[w] & ~by[w]; dy[w] = by[w] & ~bx[w]; }
+            int b = low_bit<W>(dx), d = low_bit<W>(dy);
+            int sg = (count_below<W>(R, b) + count_below<W>(R, d)) & 1;
+            info[t] = (uint32_t)rn[d] | ((uint32_t)rn[b] << 8) | ((uint32_t)(S.om2[b] + 64) << 16) |
+                      ((uint32_t)(S.oN[b] & 1) << 23) | ((uint32_t)sg << 24);
+        }
+    }
+}
+
+// Table index (<< 1) and sign bit of the two-move of each forward entry,
+// bra x -> ket y; one-moves are stored as ~(b | d << 8 | sign << 16) with b
+// in x only, d in y only.  Orbitals are offset by `base` into the
+// combined index of the pair table.
+template <int W>
+__global__ void k_fw_tb(SpeciesBuild S, int base, const int64_t *off, const int32_t *list, const int32_t *pid,
+                        const int32_t *gsize, const int64_t *goff, int ntot, int32_t *tb, int *status)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp; x < S.n_sd; x += nwarps) {
+        uint64_t bx[W];
+        load_bits<W>(S.bits, x, bx);
+        for (int64_t t = off[x] + lane; t < off[x + 1]; t += 32) {
+            uint64_t by[W], R[W], dx[W], dy[W];
+            load_bits<W>(S.bits, list[t], by);
+            int pc = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                R[w] = bx[w] & by[w]; dx[w] = bx[w] & ~by[w]; dy[w] = by[w] & ~bx[w];
+                pc += __popcll(dx[w]);
+            }
+            if (pc != 2) {                                  // one-move: ~(b | d << 8 | sign << 16)
+                const int b1 = low_bit<W>(dx), d1 = low_bit<W>(dy);
+                const int s1 = (count_below<W>(R, b1) + count_below<W>(R, d1)) & 1;
+                tb[t] = ~(int32_t)(b1 | (d1 << 8) | (s1 << 16));
+                continue;
+            }
+            int a1 = low_bit<W>(dx); dx[a1 >> 6] &= ~(1ull << (a1 & 63));
+            int a2 = low_bit<W>(dx);
+            int c1 = low_bit<W>(dy); dy[c1 >> 6] &= ~(1ull << (c1 & 63));
+            int c2 = low_bit<W>(dy);
+            int sg = (count_below<W>(R, a1) + count_below<W>(R, a2) + count_below<W>(R, c1) + count_below<W>(R, c2)) & 1;
+            int32_t e1 = pid[(base + a1) * ntot + base + a2], e2 = pid[(base + c1) * ntot + base + c2];
+            if (e1 < 0 || e2 < 0 || ((e1 ^ e2) & (0xFFF << 16))) { atomicOr(status, 4); tb[t] = -1; continue; }
+            int g = (e1 >> 16) & 0xFFF;
+            int64_t u = e1 & 0xFFFF, v = e2 & 0xFFFF;
+            if (u > v) { int64_t q = u; u = v; v = q; }
+            int64_t n = gsize[g];
+            int64_t idx = goff[g] + u * n - u * (u - 1) / 2 + (v - u);
+            tb[t] = (int32_t)((idx << 1) | sg);
+        }
+    }
+}
+
+// first one-move entry of each sub-det beyond its own class, and the size of
+// its candidate list (forward same-class entries + later-class one-moves)
+__global__ void k_later(int64_t n, const int32_t *cls_end, const int64_t *fw_off, const int64_t *n1_off,
+                        const int32_t *n1, int64_t *later, int *max_cand)
+{
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = n1_off[x], hi = n1_off[x + 1];
+        int key = cls_end[x];
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (n1[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        later[x] = lo;
+        int64_t c = (fw_off[x + 1] - fw_off[x]) + (n1_off[x + 1] - lo);
+        atomicMax(max_cand, (int)min(c, (int64_t)INT32_MAX));
+    }
+}
+
+// Candidate table of proton sub-det p (bra p -> ket q); see DevBasis.
+template <int W>
+__global__ void k_cand(SpeciesBuild S, DevBasis B, int64_t *cand_off, int32_t *colbase, int32_t *lo, int32_t *hi,
+                       uint32_t *uv, uint32_t *mv)
+{
+    const DevSpecies &SP = B.sp[0];
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int G = B.pn_G, span = B.pn_m2span;
+    for (int64_t p = warp; p < S.n_sd; p += nwarps) {
+        uint64_t pb[W];
+        load_bits<W>(S.bits, p, pb);
+        const int64_t f0 = SP.fw_off[p], nf = SP.fw_off[p + 1] - f0;
+        const int64_t l0 = SP.n1_later[p];
+        const int64_t C = nf + (SP.n1_off[p + 1] - l0);
+        const int64_t base = cand_off[p];
+        for (int64_t k = lane; k < C; k += 32) {
+            const int q = k < nf ? SP.fw[f0 + k] : SP.n1[l0 + (k - nf)];
+            uint64_t qb[W], R[W], dx[W], dy[W];
+            load_bits<W>(S.bits, q, qb);
+            int pc = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                R[w] = pb[w] & qb[w]; dx[w] = pb[w] & ~qb[w]; dy[w] = qb[w] & ~pb[w];
+                pc += __popcll(dx[w]);
+            }
+            const int l = B.nb[q];
+            colbase[base + k] = (int32_t)(B.rowbase[q] - l);
+            lo[base + k] = l;
+            if (pc == 1) {
+                const int a = low_bit<W>(dx), c = low_bit<W>(dy);
+                const int sg = (count_below<W>(R, a) + count_below<W>(R, c)) & 1;
+                const int Ka = (S.om2[a] + span) & 0xFF;       // >= 0 by the choice of span
+                hi[base + k] = l + B.nc[q];
+                uv[base + k] = (uint32_t)(a * G + Ka) | ((uint32_t)(c * G + Ka) << 16);
+                mv[base + k] = (uint32_t)Ka | ((uint32_t)(S.oN[a] & 1) << 8) | ((uint32_t)sg << 9) |
+                               ((uint32_t)a << 16) | ((uint32_t)c << 24);
+            } else {
+                hi[base + k] = (l + B.nc[q]) | (1 << 30);
+                uv[base + k] = (uint32_t)B.fw_tb[0][f0 + k];
+                mv[base + k] = 0;
+            }
+        }
+    }
+}
+
+__global__ void k_cand_count(int64_t n, const int64_t *fw_off, const int64_t *n1_off, const int64_t *later,
+                             int64_t *cnt)
+{
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        cnt[x] = (fw_off[x + 1] - fw_off[x]) + (n1_off[x + 1] - later[x]);
+}
+
+__global__ void k_row_p(int64_t np, const int64_t *rowbase, int32_t *row_p)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < np; p += nwarps)
+        for (int64_t r = rowbase[p] + lane; r < rowbase[p + 1]; r += 32) row_p[r] = (int32_t)p;
+}
+
 template <class T>
 int dev_alloc(cih_basis &b, T **p, size_t n)
 {
@@ -255,12 +420,43 @@ int build_lists(cih_basis &b, int t, SpeciesBuild &S, cudaStream_t st)
         if (hoff[x + 1] - hoff[x] > kSortTile) return fail(CIH_ERR_UNSUPPORTED, "one-move list longer than the sort tile");
     if (n > 0) count_launches(1);
     if (n > 0) k_sort_lists<<<(int)std::min<int64_t>(n, 65535), 256, 0, st>>>(cnt_n1, n1, n);
-    e = cudaGetLastError();
+    int64_t *later;
+    int *dmax;
+    if ((rc = dev_alloc(b, &later, n)) || (rc = dev_alloc(b, &dmax, 1))) return rc;
+    cudaMemsetAsync(dmax, 0, sizeof(int), st);
+    if (n > 0) {
+        count_launches(1);
+        k_later<<<grid, 256, 0, st>>>(n, S.cls_end, cnt_fw, cnt_n1, n1, later, dmax);
+    }
+    int32_t *tb;
+    if ((rc = dev_alloc(b, &tb, tot[0]))) return rc;
+    if (n > 0) {
+        count_launches(1);
+        k_fw_tb<W><<<grid, 256, 0, st>>>(S, t == 0 ? 0 : b.s[0].n_orb, cnt_fw, fw, b.dev.pid, b.dev.gsize,
+                                         b.dev.goff, b.dev.ntot, tb, b.dev_status);
+    }
+    if (t == 1) {
+        uint32_t *info;
+        int32_t *rn;
+        if ((rc = dev_alloc(b, &info, tot[1])) || (rc = upload(b, &rn, b.pn.rn, st))) return rc;
+        if (n > 0) {
+            count_launches(1);
+            k_n1_info<W><<<grid, 256, 0, st>>>(S, cnt_n1, n1, rn, info);
+        }
+        b.dev.n1_info = info;
+    }
+    int mc = 0;
+    e = cudaMemcpyAsync(&mc, dmax, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "neighbour kernels");
+    if (t == 0) b.dev.max_cand = mc;
     D.fw_off = cnt_fw;
     D.fw = fw;
     D.n1_off = cnt_n1;
     D.n1 = n1;
+    D.n1_later = later;
+    b.dev.fw_tb[t] = tb;
     return CIH_OK;
 }
 
@@ -270,6 +466,44 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
 {
     int rc;
     int W = b.W;
+    if ((rc = dev_alloc(b, &b.dev_status, 4))) return rc;
+    b.dev.queue = b.dev_status + 1;
+    if (cudaMemsetAsync(b.dev_status, 0, 4 * sizeof(int), st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "status");
+    // basis-level tables
+    int ntot = b.s[0].n_orb + b.s[1].n_orb;
+    std::vector<int8_t> orbN(ntot);
+    for (int a = 0; a < ntot; ++a) orbN[a] = (int8_t)(a < b.s[0].n_orb ? b.s[0].oN[a] : b.s[1].oN[a - b.s[0].n_orb]);
+    int32_t *d_nb, *d_nc, *d_pid, *d_gsize;
+    int64_t *d_rowbase, *d_goff;
+    int8_t *d_orbN;
+    if ((rc = upload(b, &d_nb, b.nb, st)) || (rc = upload(b, &d_nc, b.nc, st)) ||
+        (rc = upload(b, &d_rowbase, b.rowbase, st)) || (rc = upload(b, &d_orbN, orbN, st)) ||
+        (rc = upload(b, &d_pid, b.layout.pid, st)) || (rc = upload(b, &d_gsize, b.layout.gsize, st)) ||
+        (rc = upload(b, &d_goff, b.layout.goff, st)))
+        return rc;
+    b.dev.nb = d_nb;
+    b.dev.nc = d_nc;
+    b.dev.rowbase = d_rowbase;
+    b.dev.orbN = d_orbN;
+    b.dev.pid = d_pid;
+    b.dev.gsize = d_gsize;
+    b.dev.goff = d_goff;
+    b.dev.n_p = (int32_t)b.s[0].n_sd;
+    b.dev.ntot = ntot;
+    b.dev.dim = b.dim;
+    b.dev.tbme_len = b.layout.total;
+    {
+        std::vector<int8_t> m2p(std::max(b.s[0].n_orb, 1), 0), Np(std::max(b.s[0].n_orb, 1), 0);
+        for (int a = 0; a < b.s[0].n_orb; ++a) { m2p[a] = (int8_t)b.s[0].om2[a]; Np[a] = (int8_t)b.s[0].oN[a]; }
+        int16_t *d_S; int32_t *d_gs, *d_go; int8_t *d_m2p, *d_Np;
+        if ((rc = upload(b, &d_S, b.pn.S, st)) || (rc = upload(b, &d_gs, b.pn.gsize, st)) ||
+            (rc = upload(b, &d_go, b.pn.goff, st)) || (rc = upload(b, &d_m2p, m2p, st)) ||
+            (rc = upload(b, &d_Np, Np, st)))
+            return rc;
+        b.dev.pn_S = d_S; b.dev.pn_gsize = d_gs; b.dev.pn_goff = d_go; b.dev.m2p = d_m2p; b.dev.Np = d_Np;
+        b.dev.pn_G = b.pn.G;
+        b.dev.pn_m2span = b.pn.m2span;
+    }
     for (int t = 0; t < 2; ++t) {
         const Species &s = b.s[t];
         // bit strings compacted to W words
@@ -309,39 +543,51 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
 
         SpeciesBuild S{d_bits, d_N, d_M2, d_cls_end, d_lookup, d_cb, d_ce, d_oN, d_om2,
                        (int32_t)s.n_sd, s.n_orb, moff, mspan, s.Nsub_max};
+        b.sbuild[t] = S;
         if (W == 1) rc = build_lists<1>(b, t, S, st);
         else if (W == 2) rc = build_lists<2>(b, t, S, st);
         else rc = build_lists<4>(b, t, S, st);
         if (rc) return rc;
     }
-    // basis-level tables
-    int ntot = b.s[0].n_orb + b.s[1].n_orb;
-    std::vector<int8_t> orbN(ntot);
-    for (int a = 0; a < ntot; ++a) orbN[a] = (int8_t)(a < b.s[0].n_orb ? b.s[0].oN[a] : b.s[1].oN[a - b.s[0].n_orb]);
-    int32_t *d_nb, *d_nc, *d_pid, *d_gsize;
-    int64_t *d_rowbase, *d_goff;
-    int8_t *d_orbN;
-    if ((rc = upload(b, &d_nb, b.nb, st)) || (rc = upload(b, &d_nc, b.nc, st)) ||
-        (rc = upload(b, &d_rowbase, b.rowbase, st)) || (rc = upload(b, &d_orbN, orbN, st)) ||
-        (rc = upload(b, &d_pid, b.layout.pid, st)) || (rc = upload(b, &d_gsize, b.layout.gsize, st)) ||
-        (rc = upload(b, &d_goff, b.layout.goff, st)))
-        return rc;
-    b.dev.nb = d_nb;
-    b.dev.nc = d_nc;
-    b.dev.rowbase = d_rowbase;
-    b.dev.orbN = d_orbN;
-    b.dev.pid = d_pid;
-    b.dev.gsize = d_gsize;
-    b.dev.goff = d_goff;
-    b.dev.n_p = (int32_t)b.s[0].n_sd;
-    b.dev.ntot = ntot;
-    b.dev.dim = b.dim;
-    b.dev.tbme_len = b.layout.total;
     b.scan_scratch_len = scan_scratch_needed(b.dim);
     if ((rc = dev_alloc(b, &b.scan_scratch, b.scan_scratch_len))) return rc;
-    if ((rc = dev_alloc(b, &b.dev_status, 1))) return rc;
-    cudaError_t e = cudaMemsetAsync(b.dev_status, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    {
+        const int64_t np = b.s[0].n_sd;
+        int64_t *coff;
+        int32_t *row_p;
+        if ((rc = dev_alloc(b, &coff, np + 1)) || (rc = dev_alloc(b, &row_p, b.dim))) return rc;
+        int grid = grid_for(np);
+        if (np > 0) {
+            count_launches(1);
+            k_cand_count<<<grid, 256, 0, st>>>(np, b.dev.sp[0].fw_off, b.dev.sp[0].n1_off, b.dev.sp[0].n1_later, coff);
+        }
+        if ((rc = exclusive_scan_i64(coff, np, b.scan_scratch, b.scan_scratch_len, st))) return rc;
+        int64_t total = 0;
+        cudaError_t e = cudaMemcpyAsync(&total, coff + np, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "candidate count");
+        int32_t *cb, *clo, *chi;
+        uint32_t *cuv, *cmv;
+        if ((rc = dev_alloc(b, &cb, total)) || (rc = dev_alloc(b, &clo, total)) || (rc = dev_alloc(b, &chi, total)) ||
+            (rc = dev_alloc(b, &cuv, total)) || (rc = dev_alloc(b, &cmv, total)))
+            return rc;
+        if (np > 0) {
+            count_launches(2);
+            if (W == 1) k_cand<1><<<grid, 256, 0, st>>>(b.sbuild[0], b.dev, coff, cb, clo, chi, cuv, cmv);
+            else if (W == 2) k_cand<2><<<grid, 256, 0, st>>>(b.sbuild[0], b.dev, coff, cb, clo, chi, cuv, cmv);
+            else k_cand<4><<<grid, 256, 0, st>>>(b.sbuild[0], b.dev, coff, cb, clo, chi, cuv, cmv);
+            k_row_p<<<grid, 256, 0, st>>>(np, b.dev.rowbase, row_p);
+        }
+        b.dev.cand_off = coff;
+        b.dev.cand_colbase = cb;
+        b.dev.cand_lo = clo;
+        b.dev.cand_hi = chi;
+        b.dev.cand_uv = cuv;
+        b.dev.cand_mv = cmv;
+        b.dev.row_p = row_p;
+        b.dev.A = b.space.Z + b.space.N;
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "basis upload");
     return CIH_OK;
 }
