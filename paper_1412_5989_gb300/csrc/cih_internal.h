@@ -57,17 +57,26 @@ struct DevBasis {
     int32_t pn_m2span;
     int32_t max_cand;          // largest candidate list of a proton sub-det
     int *queue;                // work counter (unused by the row kernels)
-    // candidate table: for proton sub-det p, entries cand_off[p] .. cand_off[p+1]
+    // candidate table: for proton sub-det p, records cand_off[p] .. cand_off[p+1]
     // (later same-class sub-dets with one or two protons moved, then later-class
-    // sub-dets with one proton moved, ascending), structure of arrays:
+    // sub-dets with one proton moved, ascending), one int4 each:
+    //   x  column base rowbase[q] - nbeg[q]
+    //   y  directory indices of q's neutron range: start | end << 16
+    //   z  one-move: S row bases A_u | A_v << 16; two-move: table index << 1 | sign
+    //   w  bits 0..7 K_a, 8 N_a & 1, 9 sign, 16..23 a, 24..31 c (one-move only)
     const int64_t *cand_off;
-    const int32_t *cand_colbase;   // rowbase[q] - nbeg[q]
-    const int32_t *cand_lo;        // nbeg[q]
-    const int32_t *cand_hi;        // nbeg[q] + ncnt[q], two-move flag in bit 30
-    const uint32_t *cand_uv;       // one-move: S row bases A_u | A_v << 16; two-move: table index << 1 | sign
-    const uint32_t *cand_mv;       // one-move: K_a | N_a << 8 | sign << 9 | a << 16 | c << 24
+    const int4 *cand;
+    const uint8_t *cand_self;      // per record: 0 if n can never lie in q's range,
+                                   // else 1 + the largest N of a partner; bit 7 = two-move
     const int32_t *row_p;          // row -> proton sub-det
     int32_t A;                     // particles
+    // neutron one-move lists packed (neighbour, move info), and their bucket
+    // directory: for neutron n, dir[n * dir_len + 1 + rc * NL + L] = number of
+    // entries of n's one-move list in buckets <= (relative class rc, level L);
+    // dir[n * dir_len] = 0.  rc = ((2M_y - 2M_n + DM) / 2) * 2 + (N_y & 1).
+    const int2 *n1p;
+    const int16_t *dir;
+    int32_t dir_len, NL, DM;
 };
 
 // pid entry: bits 0..15 local pair index u, bits 16..27 global group id,

@@ -356,8 +356,8 @@ constexpr int w_ins = w_n1 + 128;                          // int32[32]
 constexpr int w_cb = w_ins + 128;                          // int32[32]
 constexpr int w_uv = w_cb + 128;                           // uint32[32]
 constexpr int w_mv = w_uv + 128;                           // uint32[32]
-constexpr int w_hi = w_mv + 128;                           // int32[32]
-constexpr int w_spos = w_hi + 128;                         // int32[kSlowCap]
+constexpr int w_fl = w_mv + 128;                           // int32[32] two-move flag
+constexpr int w_spos = w_fl + 128;                         // int32[kSlowCap]
 constexpr int w_scol = w_spos + kSlowCap * 4;              // int32[kSlowCap]
 constexpr int w_scode = w_scol + kSlowCap * 4;             // uint32[kSlowCap]
 constexpr int w_occ = w_scode + kSlowCap * 4;              // int16[kMaxA]
@@ -525,7 +525,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     int32_t *w_incl = sptr<int32_t>(wb, sm::w_incl), *w_n1 = sptr<int32_t>(wb, sm::w_n1);
     int32_t *w_ins = sptr<int32_t>(wb, sm::w_ins), *w_cb = sptr<int32_t>(wb, sm::w_cb);
     uint32_t *w_uv = sptr<uint32_t>(wb, sm::w_uv), *w_mv = sptr<uint32_t>(wb, sm::w_mv);
-    int32_t *w_hi = sptr<int32_t>(wb, sm::w_hi);
+    int32_t *w_fl = sptr<int32_t>(wb, sm::w_fl);
     int32_t *w_spos = sptr<int32_t>(wb, sm::w_spos), *w_scol = sptr<int32_t>(wb, sm::w_scol);
     uint32_t *w_scode = sptr<uint32_t>(wb, sm::w_scode);
     int16_t *w_occ = sptr<int16_t>(wb, sm::w_occ);
@@ -611,13 +611,9 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                                          tb >> 1, tb & 1);
                     if (slow) {
                         const int q = nslow + __popc(sm_ & lt);
-                        if (q < kSlowCap) {
-                            w_spos[q] = (int32_t)(pos + __popc(bm & lt));
-                            w_scol[q] = (int32_t)(cbp + y);
-                            w_scode[q] = (uint32_t)~tb | (1u << 31);        // neutron one-move
-                        } else {
-                            atomicOr(status, 8);
-                        }
+                        w_spos[q] = (int32_t)(pos + __popc(bm & lt));
+                        w_scol[q] = (int32_t)(cbp + y);
+                        w_scode[q] = (uint32_t)~tb | (1u << 31);            // neutron one-move
                     }
                     nslow += __popc(sm_);
                 }
@@ -628,24 +624,25 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
 
         // ---- B: candidates of p in chunks of 32
         const int64_t c0 = B.cand_off[p], c1 = B.cand_off[p + 1];
-        const int64_t n1a = SN.n1_off[n], n1b = SN.n1_off[n + 1];
-        const int64_t self_ins = lower_bound(SN.n1, n1a, n1b, n);
+        const int64_t n1a = SN.n1_off[n];
+        const int16_t *dirn = B.dir + (int64_t)n * B.dir_len;
+        const int Nn = SN.N[n];
+        const int self_rel = (int)(lower_bound(SN.n1, n1a, SN.n1_off[n + 1], n) - n1a);
         for (int64_t k0 = c0; k0 < c1; k0 += 32) {
             const int64_t k = k0 + lane;
-            int len = 0, ins = -1, hi = 0;
-            int64_t s1 = n1a;
+            int len = 0, ins = -1, s_rel = 0, two = 0;
+            int4 r = make_int4(0, 0, 0, 0);
             if (k < c1) {
-                const int lo = B.cand_lo[k];
-                hi = B.cand_hi[k];
-                const int hr = hi & 0x3FFFFFFF;
-                const bool self = n >= lo && n < hr;
-                if (hi >> 30) {
+                r = B.cand[k];
+                const int sl = B.cand_self[k];
+                const bool self = (sl & 0x7F) > Nn;                // 1 + L_q > N_n
+                two = sl >> 7;
+                if (two) {
                     len = self;
                 } else {
-                    s1 = lower_bound(SN.n1, n1a, n1b, lo);
-                    const int64_t e1 = lower_bound(SN.n1, s1, n1b, hr);
-                    len = (int)(e1 - s1) + (self ? 1 : 0);
-                    if (self) ins = (int)(min(max(self_ins, s1), e1) - s1);
+                    s_rel = dirn[r.y & 0xFFFF];
+                    len = dirn[(unsigned)r.y >> 16] - s_rel + (self ? 1 : 0);
+                    if (self) ins = self_rel - s_rel;
                 }
             }
             int incl = len;
@@ -657,14 +654,12 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
             const int T = __shfl_sync(0xffffffffu, incl, 31);
             if (MODE != 0 && T > 0) {
                 w_incl[lane] = incl;
-                w_n1[lane] = (int32_t)(s1 - n1a);
+                w_n1[lane] = s_rel;
                 w_ins[lane] = ins;
-                w_hi[lane] = hi;
-                if (k < c1) {
-                    w_cb[lane] = B.cand_colbase[k];
-                    w_uv[lane] = B.cand_uv[k];
-                    w_mv[lane] = B.cand_mv[k];
-                }
+                w_fl[lane] = two;
+                w_cb[lane] = r.x;
+                w_uv[lane] = (uint32_t)r.z;
+                w_mv[lane] = (uint32_t)r.w;
                 __syncwarp();
                 const int iters = (T + 31) >> 5;                   // same for every lane
                 for (int it = 0; it < iters; ++it) {
@@ -683,7 +678,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                         const int64_t o = out + pos + e;
                         const int64_t cb = w_cb[j];
                         const uint32_t uv = w_uv[j];
-                        if (w_hi[j] >> 30) {
+                        if (w_fl[j]) {
                             put_single<MODE>(B, F, Gr, status, o, lim, nnz, row, cb + n, (int64_t)(uv >> 1), uv & 1);
                         } else {
                             const int insj = w_ins[j];
@@ -691,24 +686,20 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                                 slow = true;
                                 colj = cb + n;
                             } else {
-                                const int64_t np = n1a + w_n1[j] + tt - ((insj >= 0 && tt > insj) ? 1 : 0);
+                                const int2 ent = B.n1p[n1a + w_n1[j] + tt - ((insj >= 0 && tt > insj) ? 1 : 0)];
                                 int sg;
-                                const int64_t idx = pn_index(sb, uv, w_mv[j], B.n1_info[np], sg);
-                                put_single<MODE>(B, F, Gr, status, o, lim, nnz, row, cb + SN.n1[np], idx, sg);
+                                const int64_t idx = pn_index(sb, uv, w_mv[j], (uint32_t)ent.y, sg);
+                                put_single<MODE>(B, F, Gr, status, o, lim, nnz, row, cb + ent.x, idx, sg);
                             }
                         }
                     }
                     const unsigned sm_ = __ballot_sync(0xffffffffu, slow);
                     if (slow) {
                         const int q = nslow + __popc(sm_ & lt);
-                        if (q < kSlowCap) {
-                            const uint32_t mv = w_mv[j];
-                            w_spos[q] = (int32_t)(pos + e);
-                            w_scol[q] = (int32_t)colj;
-                            w_scode[q] = ((mv >> 16) & 0xFF) | (((mv >> 24) & 0xFF) << 8) | (((mv >> 9) & 1) << 16);
-                        } else {
-                            atomicOr(status, 8);
-                        }
+                        const uint32_t mv = w_mv[j];
+                        w_spos[q] = (int32_t)(pos + e);
+                        w_scol[q] = (int32_t)colj;
+                        w_scode[q] = ((mv >> 16) & 0xFF) | (((mv >> 24) & 0xFF) << 8) | (((mv >> 9) & 1) << 16);
                     }
                     nslow += __popc(sm_);
                 }

@@ -284,15 +284,19 @@ __global__ void k_later(int64_t n, const int32_t *cls_end, const int64_t *fw_off
 }
 
 // Candidate table of proton sub-det p (bra p -> ket q); see DevBasis.
+// The directory indices locate q's neutron range in the one-move list of any
+// row neutron n of p: the range is the prefix N <= L_q of the class
+// (2M - 2M_q, parity of Nlim - N_q), which relative to n's class is
+// 2M_p - 2M_q.
 template <int W>
-__global__ void k_cand(SpeciesBuild S, DevBasis B, int64_t *cand_off, int32_t *colbase, int32_t *lo, int32_t *hi,
-                       uint32_t *uv, uint32_t *mv)
+__global__ void k_cand(SpeciesBuild S, DevBasis B, const int8_t *Nq, const int16_t *M2q, int Nlim, int64_t *cand_off,
+                       int4 *cand, uint8_t *cself)
 {
     const DevSpecies &SP = B.sp[0];
     int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int G = B.pn_G, span = B.pn_m2span;
+    const int G = B.pn_G, span = B.pn_m2span, NL = B.NL, DM = B.DM;
     for (int64_t p = warp; p < S.n_sd; p += nwarps) {
         uint64_t pb[W];
         load_bits<W>(S.bits, p, pb);
@@ -300,6 +304,7 @@ __global__ void k_cand(SpeciesBuild S, DevBasis B, int64_t *cand_off, int32_t *c
         const int64_t l0 = SP.n1_later[p];
         const int64_t C = nf + (SP.n1_off[p + 1] - l0);
         const int64_t base = cand_off[p];
+        const int par_p = (Nlim - Nq[p]) & 1;
         for (int64_t k = lane; k < C; k += 32) {
             const int q = k < nf ? SP.fw[f0 + k] : SP.n1[l0 + (k - nf)];
             uint64_t qb[W], R[W], dx[W], dy[W];
@@ -310,22 +315,65 @@ __global__ void k_cand(SpeciesBuild S, DevBasis B, int64_t *cand_off, int32_t *c
                 R[w] = pb[w] & qb[w]; dx[w] = pb[w] & ~qb[w]; dy[w] = qb[w] & ~pb[w];
                 pc += __popcll(dx[w]);
             }
-            const int l = B.nb[q];
-            colbase[base + k] = (int32_t)(B.rowbase[q] - l);
-            lo[base + k] = l;
+            const int Lq = Nlim - Nq[q];                       // largest N of a partner of q
+            const int par_q = Lq & 1;
+            const int dM = M2q[p] - M2q[q];
+            const int rc = ((dM + DM) >> 1) * 2 + par_q;
+            const int Lc = min(Lq, NL - 1);
+            int st = rc * NL, en = 1 + rc * NL + Lc;
+            if (dM > DM || dM < -DM || Lc < 0) st = en = 0;  // no neutron one-move reaches q's range
+            const bool same = M2q[p] == M2q[q] && par_p == par_q;    // q's range is in n's class
+            int4 r;
+            r.x = (int32_t)(B.rowbase[q] - B.nb[q]);
+            r.y = st | (en << 16);
+            uint8_t sl = same ? (uint8_t)(1 + Lq) : 0;
             if (pc == 1) {
                 const int a = low_bit<W>(dx), c = low_bit<W>(dy);
                 const int sg = (count_below<W>(R, a) + count_below<W>(R, c)) & 1;
                 const int Ka = (S.om2[a] + span) & 0xFF;       // >= 0 by the choice of span
-                hi[base + k] = l + B.nc[q];
-                uv[base + k] = (uint32_t)(a * G + Ka) | ((uint32_t)(c * G + Ka) << 16);
-                mv[base + k] = (uint32_t)Ka | ((uint32_t)(S.oN[a] & 1) << 8) | ((uint32_t)sg << 9) |
-                               ((uint32_t)a << 16) | ((uint32_t)c << 24);
+                r.z = (int32_t)((uint32_t)(a * G + Ka) | ((uint32_t)(c * G + Ka) << 16));
+                r.w = (int32_t)((uint32_t)Ka | ((uint32_t)(S.oN[a] & 1) << 8) | ((uint32_t)sg << 9) |
+                                ((uint32_t)a << 16) | ((uint32_t)c << 24));
             } else {
-                hi[base + k] = (l + B.nc[q]) | (1 << 30);
-                uv[base + k] = (uint32_t)B.fw_tb[0][f0 + k];
-                mv[base + k] = 0;
+                r.z = B.fw_tb[0][f0 + k];
+                r.w = 0;
+                sl |= 0x80;
             }
+            cand[base + k] = r;
+            cself[base + k] = sl;
+        }
+    }
+}
+
+// Pack each neutron one-move entry with its move info, and build the bucket
+// directory of each list (see DevBasis).
+__global__ void k_n1_pack(int64_t n, const int64_t *off, const int32_t *list, const uint32_t *info, int2 *packed)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < off[n]; t += (int64_t)gridDim.x * blockDim.x)
+        packed[t] = make_int2(list[t], (int)info[t]);
+}
+
+__global__ void k_dir(SpeciesBuild S, const int64_t *off, const int32_t *list, int NL, int DM, int dir_len,
+                      int16_t *dir)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp; x < S.n_sd; x += nwarps) {
+        const int64_t a0 = off[x], a1 = off[x + 1];
+        const int M0 = S.M2[x];
+        int16_t *d = dir + x * (int64_t)dir_len;
+        if (lane == 0) d[0] = 0;
+        for (int b = lane; b < dir_len - 1; b += 32) {
+            // entries with bucket key <= b: keys are non-decreasing along the sorted list
+            int64_t lo = a0, hi = a1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                const int y = list[mid];
+                const int key = (((int)S.M2[y] - M0 + DM) >> 1) * 2 * NL + (S.N[y] & 1) * NL + S.N[y];
+                if (key <= b) lo = mid + 1; else hi = mid;
+            }
+            d[1 + b] = (int16_t)(lo - a0);
         }
     }
 }
@@ -552,6 +600,35 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
     b.scan_scratch_len = scan_scratch_needed(b.dim);
     if ((rc = dev_alloc(b, &b.scan_scratch, b.scan_scratch_len))) return rc;
     {
+        // neutron one-move lists: packed entries and bucket directory
+        const Species &Q = b.s[1];
+        int dm = 0;
+        for (int x = 0; x < Q.n_orb; ++x)
+            for (int y = 0; y < Q.n_orb; ++y) dm = std::max(dm, std::abs(Q.om2[x] - Q.om2[y]));
+        const int NL = Q.Nsub_max + 1, RC = (dm + 1) * 2;
+        const int dir_len = 1 + RC * NL;
+        if (dir_len > 65535) return fail(CIH_ERR_UNSUPPORTED, "neutron bucket directory too long");
+        const int64_t nn = Q.n_sd;
+        int64_t tot = 0;
+        cudaError_t e = cudaMemcpyAsync(&tot, b.dev.sp[1].n1_off + nn, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "one-move list size");
+        int2 *n1p;
+        int16_t *dir;
+        if ((rc = dev_alloc(b, &n1p, tot)) || (rc = dev_alloc(b, &dir, (size_t)nn * dir_len))) return rc;
+        if (nn > 0) {
+            count_launches(2);
+            k_n1_pack<<<(int)std::min<int64_t>((tot + 255) / 256 + 1, 65535), 256, 0, st>>>(
+                nn, b.dev.sp[1].n1_off, b.dev.sp[1].n1, b.dev.n1_info, n1p);
+            k_dir<<<grid_for(nn), 256, 0, st>>>(b.sbuild[1], b.dev.sp[1].n1_off, b.dev.sp[1].n1, NL, dm, dir_len, dir);
+        }
+        b.dev.n1p = n1p;
+        b.dev.dir = dir;
+        b.dev.dir_len = dir_len;
+        b.dev.NL = NL;
+        b.dev.DM = dm;
+    }
+    {
         const int64_t np = b.s[0].n_sd;
         int64_t *coff;
         int32_t *row_p;
@@ -566,24 +643,20 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
         cudaError_t e = cudaMemcpyAsync(&total, coff + np, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "candidate count");
-        int32_t *cb, *clo, *chi;
-        uint32_t *cuv, *cmv;
-        if ((rc = dev_alloc(b, &cb, total)) || (rc = dev_alloc(b, &clo, total)) || (rc = dev_alloc(b, &chi, total)) ||
-            (rc = dev_alloc(b, &cuv, total)) || (rc = dev_alloc(b, &cmv, total)))
-            return rc;
+        int4 *cand;
+        uint8_t *cself;
+        if ((rc = dev_alloc(b, &cand, total)) || (rc = dev_alloc(b, &cself, total))) return rc;
         if (np > 0) {
             count_launches(2);
-            if (W == 1) k_cand<1><<<grid, 256, 0, st>>>(b.sbuild[0], b.dev, coff, cb, clo, chi, cuv, cmv);
-            else if (W == 2) k_cand<2><<<grid, 256, 0, st>>>(b.sbuild[0], b.dev, coff, cb, clo, chi, cuv, cmv);
-            else k_cand<4><<<grid, 256, 0, st>>>(b.sbuild[0], b.dev, coff, cb, clo, chi, cuv, cmv);
+            const SpeciesBuild &SB = b.sbuild[0];
+            if (W == 1) k_cand<1><<<grid, 256, 0, st>>>(SB, b.dev, SB.N, SB.M2, b.Nlim, coff, cand, cself);
+            else if (W == 2) k_cand<2><<<grid, 256, 0, st>>>(SB, b.dev, SB.N, SB.M2, b.Nlim, coff, cand, cself);
+            else k_cand<4><<<grid, 256, 0, st>>>(SB, b.dev, SB.N, SB.M2, b.Nlim, coff, cand, cself);
             k_row_p<<<grid, 256, 0, st>>>(np, b.dev.rowbase, row_p);
         }
         b.dev.cand_off = coff;
-        b.dev.cand_colbase = cb;
-        b.dev.cand_lo = clo;
-        b.dev.cand_hi = chi;
-        b.dev.cand_uv = cuv;
-        b.dev.cand_mv = cmv;
+        b.dev.cand = cand;
+        b.dev.cand_self = cself;
         b.dev.row_p = row_p;
         b.dev.A = b.space.Z + b.space.N;
     }
