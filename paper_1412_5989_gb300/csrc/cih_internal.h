@@ -70,6 +70,7 @@ struct DevBasis {
                                    // else 1 + the largest N of a partner; bit 7 = two-move
     const int32_t *row_p;          // row -> proton sub-det
     int32_t A;                     // particles
+    int32_t nZ[2];                 // particles per species
     // neutron one-move lists packed (neighbour, move info), and their bucket
     // directory: for neutron n, dir[n * dir_len + 1 + rc * NL + L] = number of
     // entries of n's one-move list in buckets <= (relative class rc, level L);
@@ -77,6 +78,8 @@ struct DevBasis {
     const int2 *n1p;
     const int16_t *dir;
     int32_t dir_len, NL, DM;
+    const int16_t *self_rel;       // per neutron n: entries of its one-move list below n
+    const uint8_t *occ[2];         // per sub-det: its occupied orbitals, ascending (Z_s each)
 };
 
 // pid entry: bits 0..15 local pair index u, bits 16..27 global group id,

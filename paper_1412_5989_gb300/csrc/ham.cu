@@ -326,13 +326,13 @@ __device__ __forceinline__ int64_t lower_bound(const int32_t *list, int64_t lo, 
 //   A         - n's forward same-class neighbours inside p's partner range:
 //               two-moves from their precomputed table index, one-moves
 //               deferred;
-//   B         - p's candidate table in chunks of 32: lane k finds its
-//               segment (n itself if inside q's range, plus n's one-move
-//               neighbours inside it, by binary search), a warp scan places
-//               the segments and the chunk's elements are emitted flattened
-//               (lane e writes element e: contiguous stores).  pp two-moves use
-//               the precomputed index, pn elements u(a,b) = S[a][kappa] + r(b),
-//               proton one-moves are deferred;
+//   B         - p's candidate records in chunks of 32: lane k reads its
+//               neutron segment from n's bucket directory (plus n itself if
+//               inside q's range), a warp scan places the segments and the
+//               chunk's elements are emitted flattened (lane e writes element
+//               e: contiguous stores).  pp two-moves use the precomputed
+//               index, pn elements u(a,b) = S[a][kappa] + r(b), proton
+//               one-moves are deferred;
 //   deferred  - one-move elements, lanes over (element, spectator) pairs and
 //               a segmented FP64 reduction.
 
@@ -350,18 +350,13 @@ constexpr int pi = goff + kGroupCap * 4;                   // uint8[kPairCap]
 constexpr int pj = pi + kPairCap;                          // uint8[kPairCap]
 constexpr int warp0 = (pj + kPairCap + 15) / 16 * 16;
 // per warp
-constexpr int w_incl = 0;                                  // int32[32]
-constexpr int w_n1 = w_incl + 128;                         // int32[32]
-constexpr int w_ins = w_n1 + 128;                          // int32[32]
-constexpr int w_cb = w_ins + 128;                          // int32[32]
-constexpr int w_uv = w_cb + 128;                           // uint32[32]
-constexpr int w_mv = w_uv + 128;                           // uint32[32]
-constexpr int w_fl = w_mv + 128;                           // int32[32] two-move flag
-constexpr int w_spos = w_fl + 128;                         // int32[kSlowCap]
+constexpr int w_seg = 0;                                   // int4[32]: colbase, uv, mv, aux
+constexpr int w_incl = w_seg + 32 * 16;                    // int32[32]
+constexpr int w_spos = w_incl + 128;                       // int32[kSlowCap]
 constexpr int w_scol = w_spos + kSlowCap * 4;              // int32[kSlowCap]
 constexpr int w_scode = w_scol + kSlowCap * 4;             // uint32[kSlowCap]
 constexpr int w_occ = w_scode + kSlowCap * 4;              // int16[kMaxA]
-constexpr int w_size = w_occ + kMaxA * 2;
+constexpr int w_size = (w_occ + kMaxA * 2 + 15) / 16 * 16;
 constexpr int S = warp0 + kWarps * w_size;                 // int16[n_orb_p * G]
 }  // namespace sm
 
@@ -377,7 +372,7 @@ __device__ __forceinline__ double warp_sum(double v, int width)
 }
 
 // table index of a pn element from the candidate (uv, mv) and neutron move (ni)
-__device__ __forceinline__ int64_t pn_index(const unsigned char *sb, uint32_t uv, uint32_t mv, uint32_t ni, int &sign)
+__device__ __forceinline__ int pn_index(const unsigned char *sb, uint32_t uv, uint32_t mv, uint32_t ni, int &sign)
 {
     const int16_t *S = reinterpret_cast<const int16_t *>(sb + sm::S);
     const int32_t *gs = reinterpret_cast<const int32_t *>(sb + sm::gsize);
@@ -387,59 +382,52 @@ __device__ __forceinline__ int64_t pn_index(const unsigned char *sb, uint32_t uv
     int u = S[(int)(uv & 0xFFFF) + t] + (int)((ni >> 8) & 0xFF);
     int v = S[(int)(uv >> 16) + t] + (int)(ni & 0xFF);
     if (u > v) { const int x = u; u = v; v = x; }
-    const int64_t n = gs[kappa];
     sign = (int)(((mv >> 9) ^ (ni >> 24)) & 1);
-    return (int64_t)go[kappa] + (int64_t)u * n - (int64_t)u * (u - 1) / 2 + (v - u);
+    return go[kappa] + u * gs[kappa] - ((u * (u - 1)) >> 1) + (v - u);
 }
 
-// one single-term element (table index, sign bit) at position o
-template <int MODE>
-__device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F, const GradArgs &Gr, int *status,
-                                           int64_t o, int64_t lim, int64_t nnz, int64_t row, int64_t colj,
-                                           int64_t idx, int sgn)
+// Row output view: column and value pointers at the row's first element.
+struct RowOut {
+    int32_t *col;
+    float *val;
+    int64_t nnz;      // value set stride
+    int64_t row;
+};
+
+// one single-term element (table index, sign bit) at row-relative position e
+template <int MODE, bool K1>
+__device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F, const GradArgs &Gr, const RowOut &R,
+                                           int e, int64_t colj, int idx, int sgn)
 {
     if (MODE == 1) {
-        if (o >= lim) { atomicOr(status, 2); return; }
-        F.col[o] = (int32_t)colj;
-        for (int k = 0; k < F.K; ++k) {
-            const float v = __ldg(F.tbme + (int64_t)k * B.tbme_len + idx);
-            F.val[(int64_t)k * nnz + o] = sgn ? -v : v;
+        R.col[e] = (int32_t)colj;
+        if (K1) {
+            const float v = __ldg(F.tbme + idx);
+            R.val[e] = sgn ? -v : v;
+        } else {
+            for (int k = 0; k < F.K; ++k) {
+                const float v = __ldg(F.tbme + (int64_t)k * B.tbme_len + idx);
+                R.val[(int64_t)k * R.nnz + e] = sgn ? -v : v;
+            }
         }
     } else if (MODE == 2) {
         for (int k = 0; k < Gr.K; ++k) {
             const double *psi = Gr.psi + (int64_t)k * B.dim;
-            const double f = 2.0 * psi[row] * psi[colj];
+            const double f = 2.0 * psi[R.row] * psi[colj];
             const long long qv = __double2ll_rn((sgn ? -f : f) * kFixScale);
             atomicAdd(Gr.acc + (int64_t)k * B.tbme_len + idx, (unsigned long long)qv);
         }
     }
 }
 
-template <int W>
-__device__ __forceinline__ int nth_bit(const uint64_t (&x)[W], int i)
-{
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        const int c = __popcll(x[w]);
-        if (i < c) {
-            uint64_t m = x[w];
-            for (int k = 0; k < i; ++k) m &= m - 1;
-            return w * 64 + __ffsll((long long)m) - 1;
-        }
-        i -= c;
-    }
-    return -1;
-}
-
 // Deferred one-move elements of a row: lanes over (element, spectator)
 // pairs, groups of the next power of two >= A-1 lanes, FP64 segmented sum.
 // The queue holds row-relative positions, columns and packed moves
 // (bra-only a, ket-only c, sign, neutron flag in bit 31).
-template <int MODE>
-__device__ __noinline__ void flush_slow(const DevBasis &B, const FillArgs &F, const GradArgs &Gr, int *status,
-                                        const int16_t *w_occ, const int32_t *w_spos, const int32_t *w_scol,
-                                        const uint32_t *w_scode, int &nslow, int64_t out, int64_t lim, int64_t nnz,
-                                        int64_t row)
+template <int MODE, bool K1>
+__device__ __forceinline__ void flush_slow(const DevBasis &B, const FillArgs &F, const GradArgs &Gr, int *status,
+                                           const int16_t *w_occ, const int32_t *w_spos, const int32_t *w_scol,
+                                           const uint32_t *w_scode, int &nslow, const RowOut &R)
 {
     const int lane = threadIdx.x & 31;
     const int A = B.A, nbase = B.sp[1].orb_base;
@@ -461,31 +449,27 @@ __device__ __noinline__ void flush_slow(const DevBasis &B, const FillArgs &F, co
         for (int x = 0; x < A; ++x) ia += (w_occ[x] < a);
         const bool has = act && i < sp_n;
         const int kspec = has ? w_occ[i + (i >= ia ? 1 : 0)] : 0;
-        const int64_t o = out + (act ? w_spos[e] : 0);
+        const int eo = act ? w_spos[e] : 0;
         const int64_t colj = act ? w_scol[e] : 0;
         int64_t idx = 0;
         int sg = 1;
         bool ok = true;
         if (has) ok = tbme_at(B, a, kspec, c, kspec, idx, sg);
         if (!ok && atomicOr(status, 1) == 0) {
-            status[2] = a | (kspec << 8) | (c << 16) | (kspec << 24);
-            status[3] = 2 | (ns << 8) | (ia << 16) | (A << 24);
+            status[2] = a | (c << 16);
+            status[3] = 2 | (kspec << 8);
         }
-        for (int kk = 0; kk < (MODE == 1 ? F.K : Gr.K); ++kk) {
+        for (int kk = 0; kk < (MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++kk) {
             if (MODE == 1) {
                 double v = 0.0;
                 if (has && ok) v = sg * (double)__ldg(F.tbme + (int64_t)kk * B.tbme_len + idx);
                 v = warp_sum(v, gsz);
                 if (act && i == 0) {
-                    if (o < lim) {
-                        if (kk == 0) F.col[o] = (int32_t)colj;
-                        F.val[(int64_t)kk * nnz + o] = (float)(sgn ? -v : v);
-                    } else {
-                        atomicOr(status, 2);
-                    }
+                    if (kk == 0) R.col[eo] = (int32_t)colj;
+                    R.val[(int64_t)kk * R.nnz + eo] = (float)(sgn ? -v : v);
                 }
             } else if (has && ok) {
-                const double f = 2.0 * Gr.psi[(int64_t)kk * B.dim + row] * Gr.psi[(int64_t)kk * B.dim + colj];
+                const double f = 2.0 * Gr.psi[(int64_t)kk * B.dim + R.row] * Gr.psi[(int64_t)kk * B.dim + colj];
                 const long long qv = __double2ll_rn((sgn ? -1 : 1) * sg * f * kFixScale);
                 atomicAdd(Gr.acc + (int64_t)kk * B.tbme_len + idx, (unsigned long long)qv);
             }
@@ -495,7 +479,7 @@ __device__ __noinline__ void flush_slow(const DevBasis &B, const FillArgs &F, co
     nslow = 0;
 }
 
-template <int W, int MODE>
+template <int W, int MODE, bool K1>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs Gr, int *status)
 {
@@ -522,15 +506,14 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     }
     const int64_t nnz = MODE == 1 ? rowptr[B.dim] : 0;
     unsigned char *wb = sb + sm::warp0 + wid * sm::w_size;
-    int32_t *w_incl = sptr<int32_t>(wb, sm::w_incl), *w_n1 = sptr<int32_t>(wb, sm::w_n1);
-    int32_t *w_ins = sptr<int32_t>(wb, sm::w_ins), *w_cb = sptr<int32_t>(wb, sm::w_cb);
-    uint32_t *w_uv = sptr<uint32_t>(wb, sm::w_uv), *w_mv = sptr<uint32_t>(wb, sm::w_mv);
-    int32_t *w_fl = sptr<int32_t>(wb, sm::w_fl);
+    int4 *w_seg = sptr<int4>(wb, sm::w_seg);
+    int32_t *w_incl = sptr<int32_t>(wb, sm::w_incl);
     int32_t *w_spos = sptr<int32_t>(wb, sm::w_spos), *w_scol = sptr<int32_t>(wb, sm::w_scol);
     uint32_t *w_scode = sptr<uint32_t>(wb, sm::w_scode);
     int16_t *w_occ = sptr<int16_t>(wb, sm::w_occ);
     const int64_t gw = (blockIdx.x * (int64_t)kThreads + tid) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+    const int Zpro = B.nZ[0], Zneu = B.nZ[1];
 
     for (int64_t row = gw; row < B.dim; row += nw) {
         const int p = B.row_p[row];
@@ -539,30 +522,33 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         const int n = nbp + (int)(row - rbp);
         const int nend = nbp + B.nc[p];
         const int64_t cbp = rbp - nbp;
-        const int64_t out = MODE == 1 ? rowptr[row] : 0;
-        const int64_t lim = MODE == 1 ? min(rowptr[row + 1], nnz) : 0;
+        RowOut R;
+        R.row = row;
+        R.nnz = nnz;
+        int rowlen = 0;
+        if (MODE == 1) {
+            const int64_t r0 = rowptr[row];
+            rowlen = (int)(min(rowptr[row + 1], nnz) - r0);
+            R.col = F.col + r0;
+            R.val = F.val + r0;
+        }
         int nslow = 0;
 
         // ---- diagonal: occupied orbitals (combined, ascending), then all pairs
         if (MODE != 0) {
-            uint64_t pb[W], nbits[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) { pb[w] = SP.bits[(int64_t)p * W + w]; nbits[w] = SN.bits[(int64_t)n * W + w]; }
-            int zp = 0;
-#pragma unroll
-            for (int w = 0; w < W; ++w) zp += __popcll(pb[w]);
             for (int i = lane; i < A; i += 32)
-                w_occ[i] = (int16_t)(i < zp ? nth_bit<W>(pb, i) : nbase + nth_bit<W>(nbits, i - zp));
+                w_occ[i] = i < Zpro ? (int16_t)B.occ[0][(int64_t)p * Zpro + i]
+                                    : (int16_t)(nbase + B.occ[1][(int64_t)n * Zneu + (i - Zpro)]);
             __syncwarp();
             const uint8_t *pi = sptr<uint8_t>(sb, sm::pi), *pj = sptr<uint8_t>(sb, sm::pj);
-            for (int k = 0; k < (MODE == 1 ? F.K : Gr.K); ++k) {
+            for (int k = 0; k < (MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++k) {
                 double acc = 0.0;
                 for (int l = lane; l < npairs; l += 32) {
                     const int a = w_occ[pi[l]], c = w_occ[pj[l]];
                     int64_t idx;
                     int sg;
                     if (!tbme_at(B, a, c, a, c, idx, sg)) {
-                        if (atomicOr(status, 1) == 0) { status[2] = a | (c << 8) | (a << 16) | (c << 24); status[3] = 1; }
+                        if (atomicOr(status, 1) == 0) { status[2] = a | (c << 16); status[3] = 1; }
                         continue;
                     }
                     if (MODE == 1) {
@@ -579,18 +565,14 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                         acc += F.esp ? F.esp[a] : F.hw * ((double)B.orbN[a] + 1.5);
                     }
                     acc = warp_sum(acc, 32);
-                    if (lane == 0) {
-                        if (out < lim) {
-                            if (k == 0) F.col[out] = (int32_t)row;
-                            F.val[(int64_t)k * nnz + out] = (float)acc;
-                        } else {
-                            atomicOr(status, 2);
-                        }
+                    if (lane == 0 && rowlen > 0) {
+                        if (k == 0) R.col[0] = (int32_t)row;
+                        R.val[(int64_t)k * nnz] = (float)acc;
                     }
                 }
             }
         }
-        int64_t pos = 1;
+        int pos = 1;
 
         // ---- A: same-class forward neutron neighbours inside p's range
         {
@@ -601,21 +583,21 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 const bool in = y < nend;
                 const unsigned bm = __ballot_sync(0xffffffffu, in);
                 if (MODE != 0) {
+                    if (MODE == 1 && pos + __popc(bm) > rowlen) { atomicOr(status, 2); break; }
                     if (nslow > kSlowCap - 32)
-                        flush_slow<MODE>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, out, lim, nnz, row);
+                        flush_slow<MODE, K1>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
                     const int32_t tb = in ? B.fw_tb[1][t] : 0;
                     const bool slow = in && tb < 0;
-                    const unsigned sm_ = __ballot_sync(0xffffffffu, slow);
-                    if (in && !slow)
-                        put_single<MODE>(B, F, Gr, status, out + pos + __popc(bm & lt), lim, nnz, row, cbp + y,
-                                         tb >> 1, tb & 1);
+                    const unsigned smk = __ballot_sync(0xffffffffu, slow);
+                    const int e = pos + __popc(bm & lt);
+                    if (in && !slow) put_single<MODE, K1>(B, F, Gr, R, e, cbp + y, tb >> 1, tb & 1);
                     if (slow) {
-                        const int q = nslow + __popc(sm_ & lt);
-                        w_spos[q] = (int32_t)(pos + __popc(bm & lt));
+                        const int q = nslow + __popc(smk & lt);
+                        w_spos[q] = e;
                         w_scol[q] = (int32_t)(cbp + y);
                         w_scode[q] = (uint32_t)~tb | (1u << 31);            // neutron one-move
                     }
-                    nslow += __popc(sm_);
+                    nslow += __popc(smk);
                 }
                 pos += __popc(bm);
                 if (bm != 0xffffffffu) break;
@@ -627,7 +609,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         const int64_t n1a = SN.n1_off[n];
         const int16_t *dirn = B.dir + (int64_t)n * B.dir_len;
         const int Nn = SN.N[n];
-        const int self_rel = (int)(lower_bound(SN.n1, n1a, SN.n1_off[n + 1], n) - n1a);
+        const int self_rel = B.self_rel[n];
         for (int64_t k0 = c0; k0 < c1; k0 += 32) {
             const int64_t k = k0 + lane;
             int len = 0, ins = -1, s_rel = 0, two = 0;
@@ -653,62 +635,55 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
             }
             const int T = __shfl_sync(0xffffffffu, incl, 31);
             if (MODE != 0 && T > 0) {
+                if (MODE == 1 && pos + T > rowlen) { atomicOr(status, 2); pos += T; continue; }
                 w_incl[lane] = incl;
-                w_n1[lane] = s_rel;
-                w_ins[lane] = ins;
-                w_fl[lane] = two;
-                w_cb[lane] = r.x;
-                w_uv[lane] = (uint32_t)r.z;
-                w_mv[lane] = (uint32_t)r.w;
+                w_seg[lane] = make_int4(r.x, r.z, r.w, s_rel | ((ins + 1) << 16) | (two << 31));
                 __syncwarp();
                 const int iters = (T + 31) >> 5;                   // same for every lane
                 for (int it = 0; it < iters; ++it) {
                     if (nslow > kSlowCap - 32)
-                        flush_slow<MODE>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, out, lim, nnz, row);
+                        flush_slow<MODE, K1>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
                     const int e = (it << 5) + lane;
-                    const bool act = e < T;
                     int j = 0;
 #pragma unroll
                     for (int step = 16; step > 0; step >>= 1)
                         if (w_incl[j + step - 1] <= e) j += step;
                     bool slow = false;
-                    int64_t colj = 0;
-                    if (act) {
+                    uint32_t code = 0;
+                    if (e < T) {
                         const int tt = e - (j ? w_incl[j - 1] : 0);
-                        const int64_t o = out + pos + e;
-                        const int64_t cb = w_cb[j];
-                        const uint32_t uv = w_uv[j];
-                        if (w_fl[j]) {
-                            put_single<MODE>(B, F, Gr, status, o, lim, nnz, row, cb + n, (int64_t)(uv >> 1), uv & 1);
+                        const int4 sg4 = w_seg[j];
+                        const int64_t cb = sg4.x;
+                        const uint32_t uv = (uint32_t)sg4.y, mv = (uint32_t)sg4.z, aux = (uint32_t)sg4.w;
+                        if (aux >> 31) {
+                            put_single<MODE, K1>(B, F, Gr, R, pos + e, cb + n, (int)(uv >> 1), uv & 1);
                         } else {
-                            const int insj = w_ins[j];
+                            const int insj = (int)((aux >> 16) & 0x7FFF) - 1;
                             if (tt == insj) {
                                 slow = true;
-                                colj = cb + n;
+                                code = ((mv >> 16) & 0xFF) | (((mv >> 24) & 0xFF) << 8) | (((mv >> 9) & 1) << 16);
                             } else {
-                                const int2 ent = B.n1p[n1a + w_n1[j] + tt - ((insj >= 0 && tt > insj) ? 1 : 0)];
+                                const int2 ent = B.n1p[n1a + (aux & 0xFFFF) + tt - ((insj >= 0 && tt > insj) ? 1 : 0)];
                                 int sg;
-                                const int64_t idx = pn_index(sb, uv, w_mv[j], (uint32_t)ent.y, sg);
-                                put_single<MODE>(B, F, Gr, status, o, lim, nnz, row, cb + ent.x, idx, sg);
+                                const int idx = pn_index(sb, uv, mv, (uint32_t)ent.y, sg);
+                                put_single<MODE, K1>(B, F, Gr, R, pos + e, cb + ent.x, idx, sg);
                             }
                         }
                     }
-                    const unsigned sm_ = __ballot_sync(0xffffffffu, slow);
+                    const unsigned smk = __ballot_sync(0xffffffffu, slow);
                     if (slow) {
-                        const int q = nslow + __popc(sm_ & lt);
-                        const uint32_t mv = w_mv[j];
-                        w_spos[q] = (int32_t)(pos + e);
-                        w_scol[q] = (int32_t)colj;
-                        w_scode[q] = ((mv >> 16) & 0xFF) | (((mv >> 24) & 0xFF) << 8) | (((mv >> 9) & 1) << 16);
+                        const int q = nslow + __popc(smk & lt);
+                        w_spos[q] = pos + e;
+                        w_scol[q] = (int32_t)((int64_t)w_seg[j].x + n);
+                        w_scode[q] = code;
                     }
-                    nslow += __popc(sm_);
+                    nslow += __popc(smk);
                 }
                 __syncwarp();
             }
             pos += T;
         }
-
-        if (MODE != 0 && nslow > 0) flush_slow<MODE>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, out, lim, nnz, row);
+        if (MODE != 0 && nslow > 0) flush_slow<MODE, K1>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
         if (MODE == 0 && lane == 0) counts[row] = pos;
         __syncwarp();
     }
@@ -722,6 +697,7 @@ int launch_rows(const cih_basis &b, const int64_t *rowptr, int64_t *counts, cons
     const DevBasis &D = b.dev;
     if (D.pn_G > kGroupCap || D.A > kMaxA || D.A - 1 > 32)
         return fail(CIH_ERR_UNSUPPORTED, "more than 33 particles or pn groups above the row kernel's capacity");
+    if (D.tbme_len > INT32_MAX) return fail(CIH_ERR_UNSUPPORTED, "two-body table above 2^31 entries");
     const size_t smem = MODE == 0 ? (size_t)sm::S : smem_bytes(D.sp[0].n_orb * D.pn_G);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -738,9 +714,10 @@ int launch_rows(const cih_basis &b, const int64_t *rowptr, int64_t *counts, cons
         ee = cudaGetLastError();
         return ee == cudaSuccess ? CIH_OK : cuda_fail(ee, "row kernel launch");
     };
-    if (b.W == 1) return go(k_rows<1, MODE>);
-    if (b.W == 2) return go(k_rows<2, MODE>);
-    return go(k_rows<4, MODE>);
+    const bool k1 = MODE == 1 && F.K == 1;
+    if (b.W == 1) return k1 ? go(k_rows<1, MODE, true>) : go(k_rows<1, MODE, false>);
+    if (b.W == 2) return k1 ? go(k_rows<2, MODE, true>) : go(k_rows<2, MODE, false>);
+    return k1 ? go(k_rows<4, MODE, true>) : go(k_rows<4, MODE, false>);
 }
 
 __global__ void k_fix_to_double(int64_t n, const unsigned long long *acc, double *out)

@@ -345,6 +345,32 @@ __global__ void k_cand(SpeciesBuild S, DevBasis B, const int8_t *Nq, const int16
     }
 }
 
+// occupied orbitals of each sub-det, ascending; and for the neutron lists the
+// number of one-move entries below the sub-det itself
+template <int W>
+__global__ void k_occ(SpeciesBuild S, int Z, const int64_t *n1_off, const int32_t *n1, uint8_t *occ, int16_t *self_rel)
+{
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < S.n_sd; x += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        for (int w = 0; w < W; ++w) {
+            uint64_t m = S.bits[x * W + w];
+            while (m) {
+                occ[x * Z + k++] = (uint8_t)(w * 64 + __ffsll((long long)m) - 1);
+                m &= m - 1;
+            }
+        }
+        if (self_rel) {
+            int64_t lo = n1_off[x], hi = n1_off[x + 1];
+            const int64_t a0 = lo;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (n1[mid] < x) lo = mid + 1; else hi = mid;
+            }
+            self_rel[x] = (int16_t)(lo - a0);
+        }
+    }
+}
+
 // Pack each neutron one-move entry with its move info, and build the bucket
 // directory of each list (see DevBasis).
 __global__ void k_n1_pack(int64_t n, const int64_t *off, const int32_t *list, const uint32_t *info, int2 *packed)
@@ -622,6 +648,27 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
                 nn, b.dev.sp[1].n1_off, b.dev.sp[1].n1, b.dev.n1_info, n1p);
             k_dir<<<grid_for(nn), 256, 0, st>>>(b.sbuild[1], b.dev.sp[1].n1_off, b.dev.sp[1].n1, NL, dm, dir_len, dir);
         }
+        int16_t *srel;
+        uint8_t *occp, *occn;
+        if ((rc = dev_alloc(b, &srel, nn)) || (rc = dev_alloc(b, &occp, (size_t)b.s[0].n_sd * std::max(b.s[0].Z, 1))) ||
+            (rc = dev_alloc(b, &occn, (size_t)nn * std::max(Q.Z, 1))))
+            return rc;
+        const int g0 = (int)std::min<int64_t>((b.s[0].n_sd + 255) / 256 + 1, 65535);
+        const int g1 = (int)std::min<int64_t>((nn + 255) / 256 + 1, 65535);
+        count_launches(2);
+        if (W == 1) {
+            k_occ<1><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
+            k_occ<1><<<g1, 256, 0, st>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
+        } else if (W == 2) {
+            k_occ<2><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
+            k_occ<2><<<g1, 256, 0, st>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
+        } else {
+            k_occ<4><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
+            k_occ<4><<<g1, 256, 0, st>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
+        }
+        b.dev.self_rel = srel;
+        b.dev.occ[0] = occp;
+        b.dev.occ[1] = occn;
         b.dev.n1p = n1p;
         b.dev.dir = dir;
         b.dev.dir_len = dir_len;
@@ -659,6 +706,8 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
         b.dev.cand_self = cself;
         b.dev.row_p = row_p;
         b.dev.A = b.space.Z + b.space.N;
+        b.dev.nZ[0] = b.space.Z;
+        b.dev.nZ[1] = b.space.N;
     }
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "basis upload");
