@@ -352,7 +352,8 @@ constexpr int warp0 = (pj + kPairCap + 15) / 16 * 16;
 // per warp
 constexpr int w_seg = 0;                                   // int4[32]: colbase, uv, mv, aux
 constexpr int w_incl = w_seg + 32 * 16;                    // int32[32]
-constexpr int w_spos = w_incl + 128;                       // int32[kSlowCap]
+constexpr int w_n1s = w_incl + 128;                        // int32[32]
+constexpr int w_spos = w_n1s + 128;                       // int32[kSlowCap]
 constexpr int w_scol = w_spos + kSlowCap * 4;              // int32[kSlowCap]
 constexpr int w_scode = w_scol + kSlowCap * 4;             // uint32[kSlowCap]
 constexpr int w_occ = w_scode + kSlowCap * 4;              // int16[kMaxA]
@@ -507,7 +508,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     const int64_t nnz = MODE == 1 ? rowptr[B.dim] : 0;
     unsigned char *wb = sb + sm::warp0 + wid * sm::w_size;
     int4 *w_seg = sptr<int4>(wb, sm::w_seg);
-    int32_t *w_incl = sptr<int32_t>(wb, sm::w_incl);
+    int32_t *w_incl = sptr<int32_t>(wb, sm::w_incl), *w_n1s = sptr<int32_t>(wb, sm::w_n1s);
     int32_t *w_spos = sptr<int32_t>(wb, sm::w_spos), *w_scol = sptr<int32_t>(wb, sm::w_scol);
     uint32_t *w_scode = sptr<uint32_t>(wb, sm::w_scode);
     int16_t *w_occ = sptr<int16_t>(wb, sm::w_occ);
@@ -604,82 +605,86 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
             }
         }
 
-        // ---- B: candidates of p in chunks of 32
+        // ---- B: candidates of p in chunks of 32 (records of the next chunk
+        //      are loaded while the current one is emitted)
         const int64_t c0 = B.cand_off[p], c1 = B.cand_off[p + 1];
         const int64_t n1a = SN.n1_off[n];
         const int16_t *dirn = B.dir + (int64_t)n * B.dir_len;
         const int Nn = SN.N[n];
         const int self_rel = B.self_rel[n];
+        int4 rn_ = make_int4(0, 0, 0, 0);
+        int sln = 0;
+        if (c0 + lane < c1) { rn_ = B.cand[c0 + lane]; sln = B.cand_self[c0 + lane]; }
         for (int64_t k0 = c0; k0 < c1; k0 += 32) {
-            const int64_t k = k0 + lane;
-            int len = 0, ins = -1, s_rel = 0, two = 0;
-            int4 r = make_int4(0, 0, 0, 0);
-            if (k < c1) {
-                r = B.cand[k];
-                const int sl = B.cand_self[k];
-                const bool self = (sl & 0x7F) > Nn;                // 1 + L_q > N_n
-                two = sl >> 7;
-                if (two) {
-                    len = self;
-                } else {
-                    s_rel = dirn[r.y & 0xFFFF];
-                    len = dirn[(unsigned)r.y >> 16] - s_rel + (self ? 1 : 0);
-                    if (self) ins = self_rel - s_rel;
-                }
+            const bool valid = k0 + lane < c1;
+            const int4 r = rn_;
+            const int sl = valid ? sln : 0;
+            if (k0 + 32 + lane < c1) { rn_ = B.cand[k0 + 32 + lane]; sln = B.cand_self[k0 + 32 + lane]; }
+            // this lane's candidate: pn neutron moves [s_rel, s_rel + lpn) of n's list,
+            // plus n itself (a pp two-move or a one-proton move) if inside q's range
+            const bool self = (sl & 0x7F) > Nn;                    // 1 + L_q > N_n
+            const int two = sl >> 7;
+            int lpn = 0, s_rel = 0;
+            if (valid && !two) {
+                s_rel = dirn[r.y & 0xFFFF];
+                lpn = dirn[(unsigned)r.y >> 16] - s_rel;
             }
-            int incl = len;
+            const int ltot = lpn + (self ? 1 : 0);
+            // one scan of both counts: pn elements in the low half, all in the high half
+            int incl = lpn | (ltot << 16);
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const int o2 = __shfl_up_sync(0xffffffffu, incl, d);
                 if (lane >= d) incl += o2;
             }
-            const int T = __shfl_sync(0xffffffffu, incl, 31);
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            const int T = tot >> 16, Tpn = tot & 0xFFFF;
             if (MODE != 0 && T > 0) {
                 if (MODE == 1 && pos + T > rowlen) { atomicOr(status, 2); pos += T; continue; }
-                w_incl[lane] = incl;
-                w_seg[lane] = make_int4(r.x, r.z, r.w, s_rel | ((ins + 1) << 16) | (two << 31));
-                __syncwarp();
-                const int iters = (T + 31) >> 5;                   // same for every lane
-                for (int it = 0; it < iters; ++it) {
-                    if (nslow > kSlowCap - 32)
-                        flush_slow<MODE, K1>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
-                    const int e = (it << 5) + lane;
-                    int j = 0;
+                const int ex_all = pos + (incl >> 16) - ltot;           // row position of the segment
+                const int ins = self && !two ? self_rel - s_rel : -1;    // where n sorts among the pn moves
+                // n itself: written by its candidate's lane
+                if (self && two) {
+                    put_single<MODE, K1>(B, F, Gr, R, ex_all, (int64_t)r.x + n, (int)((uint32_t)r.z >> 1), r.z & 1);
+                }
+                const bool p1 = self && !two;
+                const unsigned smk = __ballot_sync(0xffffffffu, p1);
+                if (nslow + __popc(smk) > kSlowCap)
+                    flush_slow<MODE, K1>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
+                if (p1) {
+                    const int q = nslow + __popc(smk & lt);
+                    const uint32_t mv = (uint32_t)r.w;
+                    w_spos[q] = ex_all + ins;
+                    w_scol[q] = (int32_t)((int64_t)r.x + n);
+                    w_scode[q] = ((mv >> 16) & 0xFF) | (((mv >> 24) & 0xFF) << 8) | (((mv >> 9) & 1) << 16);
+                }
+                nslow += __popc(smk);
+                if (Tpn > 0) {
+                    w_incl[lane] = incl & 0xFFFF;
+                    w_seg[lane] = make_int4(r.x, r.z, r.w, ex_all);
+                    w_n1s[lane] = s_rel | ((ins + 1) << 16);      // both below 2^15 (sort tile)
+                    __syncwarp();
+                    const int iters = (Tpn + 31) >> 5;
+                    for (int it = 0; it < iters; ++it) {
+                        const int e = (it << 5) + lane;
+                        if (e < Tpn) {
+                            int j = 0;
 #pragma unroll
-                    for (int step = 16; step > 0; step >>= 1)
-                        if (w_incl[j + step - 1] <= e) j += step;
-                    bool slow = false;
-                    uint32_t code = 0;
-                    if (e < T) {
-                        const int tt = e - (j ? w_incl[j - 1] : 0);
-                        const int4 sg4 = w_seg[j];
-                        const int64_t cb = sg4.x;
-                        const uint32_t uv = (uint32_t)sg4.y, mv = (uint32_t)sg4.z, aux = (uint32_t)sg4.w;
-                        if (aux >> 31) {
-                            put_single<MODE, K1>(B, F, Gr, R, pos + e, cb + n, (int)(uv >> 1), uv & 1);
-                        } else {
-                            const int insj = (int)((aux >> 16) & 0x7FFF) - 1;
-                            if (tt == insj) {
-                                slow = true;
-                                code = ((mv >> 16) & 0xFF) | (((mv >> 24) & 0xFF) << 8) | (((mv >> 9) & 1) << 16);
-                            } else {
-                                const int2 ent = B.n1p[n1a + (aux & 0xFFFF) + tt - ((insj >= 0 && tt > insj) ? 1 : 0)];
-                                int sg;
-                                const int idx = pn_index(sb, uv, mv, (uint32_t)ent.y, sg);
-                                put_single<MODE, K1>(B, F, Gr, R, pos + e, cb + ent.x, idx, sg);
-                            }
+                            for (int step = 16; step > 0; step >>= 1)
+                                if (w_incl[j + step - 1] <= e) j += step;
+                            const int tt = e - (j ? w_incl[j - 1] : 0);
+                            const int4 sg4 = w_seg[j];
+                            const int nsj = w_n1s[j];
+                            const int insj = (nsj >> 16) - 1;
+                            const int at = sg4.w + tt + ((insj >= 0 && tt >= insj) ? 1 : 0);
+                            const int2 ent = B.n1p[n1a + (nsj & 0xFFFF) + tt];
+                            int sg;
+                            const int idx = pn_index(sb, (uint32_t)sg4.y, (uint32_t)sg4.z, (uint32_t)ent.y, sg);
+                            put_single<MODE, K1>(B, F, Gr, R, at, (int64_t)sg4.x + ent.x, idx, sg);
                         }
                     }
-                    const unsigned smk = __ballot_sync(0xffffffffu, slow);
-                    if (slow) {
-                        const int q = nslow + __popc(smk & lt);
-                        w_spos[q] = pos + e;
-                        w_scol[q] = (int32_t)((int64_t)w_seg[j].x + n);
-                        w_scode[q] = code;
-                    }
-                    nslow += __popc(smk);
+                    __syncwarp();
                 }
-                __syncwarp();
             }
             pos += T;
         }
