@@ -10,10 +10,10 @@
 // bucketed by (2M, parity, N) with a stable counting sort, which yields the
 // (2M, N mod 2, N, bits) order in linear time.
 #include <algorithm>
+#include <thread>
 #include <climits>
 #include <cstdint>
 #include <cstdlib>
-#include <map>
 #include <utility>
 
 #include "cih_internal.h"
@@ -50,63 +50,118 @@ void make_orbitals(Species &s, int top_shell)
     s.n_orb = (int)s.oN.size();
 }
 
-struct Colex {
+// Sub-determinants of one species in (2M, N mod 2, N, bits) order, in two
+// parallel passes over the highest occupied orbital `top`: pass 1 counts the
+// subsets of each (top, bucket) with bucket = (2M, N mod 2, N); a prefix sum in
+// (bucket, top) order gives each pair its slot; pass 2 writes every subset to
+// its slot.  Inside one (top, bucket) the recursion visits subsets in
+// ascending bit-string order (colexicographic: highest element first), and
+// slots of the same bucket are ordered by top, so each bucket comes out
+// sorted by the bit string read as an unsigned integer.
+struct Enumerator {
     const Species &s;
     std::vector<int> minsum;      // quanta of the c lowest orbitals
-    uint64_t w[kMaxWords] = {0, 0, 0, 0};
-    std::vector<uint64_t> bits;
-    std::vector<int> N, M2;
+    int Mabs = 0, nN = 0;
 
-    explicit Colex(const Species &sp) : s(sp)
+    explicit Enumerator(const Species &sp) : s(sp)
     {
         minsum.assign(s.Z + 1, 0);
         for (int c = 1; c <= s.Z; ++c) minsum[c] = minsum[c - 1] + s.oN[c - 1];
+        std::vector<int> m(s.om2.begin(), s.om2.end());
+        for (int &x : m) x = std::abs(x);
+        std::sort(m.rbegin(), m.rend());
+        for (int c = 0; c < s.Z && c < (int)m.size(); ++c) Mabs += m[c];
+        nN = s.Nsub_max + 1;
     }
+    int64_t nkeys() const { return (int64_t)(2 * Mabs + 1) * 2 * nN; }
+    int64_t key(int N, int M) const { return ((int64_t)(M + Mabs) * 2 + (N & 1)) * nN + N; }
 
-    // c more orbitals, all below `lim`, with at most `budget` quanta
-    void rec(int c, int lim, int budget, int Nacc, int Macc)
+    // c more orbitals below `lim` with at most `budget` quanta; F(w, N, M) at each leaf
+    template <class Fn>
+    void rec(uint64_t *w, int c, int lim, int budget, int Nacc, int Macc, Fn &f) const
     {
-        if (c == 0) {
-            bits.insert(bits.end(), w, w + kMaxWords);
-            N.push_back(Nacc);
-            M2.push_back(Macc);
-            return;
-        }
+        if (c == 0) { f(w, Nacc, Macc); return; }
         for (int a = c - 1; a < lim; ++a) {
             if (s.oN[a] + minsum[c - 1] > budget) break;     // orbitals sorted by N
             w[a >> 6] |= 1ull << (a & 63);
-            rec(c - 1, a, budget - s.oN[a], Nacc + s.oN[a], Macc + s.om2[a]);
+            rec(w, c - 1, a, budget - s.oN[a], Nacc + s.oN[a], Macc + s.om2[a], f);
             w[a >> 6] &= ~(1ull << (a & 63));
         }
     }
 };
 
-// stable counting sort of the generated sub-dets by (2M, N mod 2, N)
-void bucket_sort(Species &s, Colex &g)
+template <class Fn>
+void parallel_tops(int ntop, Fn &&fn)
 {
-    int64_t n = (int64_t)g.N.size();
-    int Mabs = 0;
-    for (int m : g.M2) Mabs = std::max(Mabs, std::abs(m));
-    int nN = s.Nsub_max + 1;
-    auto key = [&](int64_t i) {
-        return ((int64_t)(g.M2[i] + Mabs) * 2 + (g.N[i] & 1)) * nN + g.N[i];
-    };
-    int64_t nkeys = (int64_t)(2 * Mabs + 1) * 2 * nN;
-    std::vector<int64_t> start(nkeys + 1, 0);
-    for (int64_t i = 0; i < n; ++i) start[key(i) + 1]++;
-    for (int64_t k = 0; k < nkeys; ++k) start[k + 1] += start[k];
-    std::vector<int64_t> order(n);
-    for (int64_t i = 0; i < n; ++i) order[start[key(i)]++] = i;
-    s.n_sd = n;
-    s.bits.resize((size_t)n * kMaxWords);
-    s.N.resize(n);
-    s.M2.resize(n);
-    for (int64_t r = 0; r < n; ++r) {
-        int64_t i = order[r];
-        std::copy(&g.bits[i * kMaxWords], &g.bits[i * kMaxWords] + kMaxWords, &s.bits[r * kMaxWords]);
-        s.N[r] = g.N[i];
-        s.M2[r] = g.M2[i];
+    unsigned hw = std::max(1u, std::min(4u, std::thread::hardware_concurrency()));
+    if (const char *e = std::getenv("CIH_THREADS")) hw = (unsigned)std::max(1, std::atoi(e));
+    int nt = (int)std::min<unsigned>(hw, (unsigned)std::max(ntop / 4, 1));
+    if (nt <= 1) { for (int t = 0; t < ntop; ++t) fn(t); return; }
+    std::vector<std::thread> th;
+    for (int i = 0; i < nt; ++i)
+        th.emplace_back([&, i]() { for (int t = i; t < ntop; t += nt) fn(t); });
+    for (auto &x : th) x.join();
+}
+
+void enumerate_subdets(Species &s)
+{
+    if (s.Z == 0) {                               // the empty sub-determinant
+        s.n_sd = 1;
+        s.bits.assign(kMaxWords, 0);
+        s.N.assign(1, 0);
+        s.M2.assign(1, 0);
+        return;
     }
+    Timer tm("enumerate");
+    Enumerator E(s);
+    const int budget = s.Nsub_max;
+    std::vector<int> tops;
+    for (int a = s.Z - 1; a < s.n_orb; ++a)
+        if (s.oN[a] + E.minsum[s.Z - 1] <= budget) tops.push_back(a);
+    const int ntop = (int)tops.size();
+    const int64_t nk = E.nkeys();
+    std::vector<int64_t> cnt((size_t)ntop * nk, 0);        // [top][bucket]: one row per thread's top
+    parallel_tops(ntop, [&](int t) {
+        uint64_t w[kMaxWords] = {0, 0, 0, 0};
+        const int a = tops[t];
+        w[a >> 6] |= 1ull << (a & 63);
+        int64_t *c = &cnt[(size_t)t * nk];
+        auto f = [&](const uint64_t *, int N, int M) { c[E.key(N, M)]++; };
+        E.rec(w, s.Z - 1, a, budget - s.oN[a], s.oN[a], s.om2[a], f);
+    });
+    tm.mark("count pass");
+    // slots in (bucket, top) order
+    // slot of (top t, bucket k) = start of bucket k + counts of lower tops in k
+    std::vector<int64_t> run(nk, 0);
+    for (int t = 0; t < ntop; ++t)
+        for (int64_t k = 0; k < nk; ++k) run[k] += cnt[(size_t)t * nk + k];
+    int64_t total = 0;
+    for (int64_t k = 0; k < nk; ++k) { const int64_t v = run[k]; run[k] = total; total += v; }
+    for (int t = 0; t < ntop; ++t)
+        for (int64_t k = 0; k < nk; ++k) {
+            const int64_t v = cnt[(size_t)t * nk + k];
+            cnt[(size_t)t * nk + k] = run[k];
+            run[k] += v;
+        }
+    run.assign(1, total);
+    tm.mark("prefix");
+    s.n_sd = total;
+    s.bits.assign((size_t)total * kMaxWords, 0);
+    s.N.assign(total, 0);
+    s.M2.assign(total, 0);
+    parallel_tops(ntop, [&](int t) {
+        uint64_t w[kMaxWords] = {0, 0, 0, 0};
+        const int a = tops[t];
+        w[a >> 6] |= 1ull << (a & 63);
+        int64_t *slot = &cnt[(size_t)t * nk];
+        auto f = [&](const uint64_t *wb, int N, int M) {
+            const int64_t i = slot[E.key(N, M)]++;
+            std::copy(wb, wb + kMaxWords, &s.bits[(size_t)i * kMaxWords]);
+            s.N[i] = N;
+            s.M2[i] = M;
+        };
+        E.rec(w, s.Z - 1, a, budget - s.oN[a], s.oN[a], s.om2[a], f);
+    });
 }
 
 void keep_only(Species &s, const std::vector<char> &keep)
@@ -166,20 +221,26 @@ int build_layout(cih_basis &b)
         int limit = b.Nlim - (a0 + a1);
         int alo = c == 1 ? P.n_orb : 0, ahi = c == 0 ? P.n_orb : (c == 1 ? ntot : P.n_orb);
         int blo = c == 0 ? 0 : P.n_orb, bhi = c == 0 ? P.n_orb : ntot;
-        std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> groups;
+        // groups keyed (2M_pair, parity), ascending: dense key (2M_pair + mspan) * 2 + parity
+        int mspan = 0;
+        for (int a = alo; a < ahi; ++a) mspan = std::max(mspan, std::abs(orbM(a)));
+        for (int bb = blo; bb < bhi; ++bb) mspan = std::max(mspan, std::abs(orbM(bb)));
+        mspan *= 2;
+        std::vector<std::vector<std::pair<int, int>>> groups((size_t)(2 * mspan + 1) * 2);
         for (int a = alo; a < ahi; ++a)
             for (int bb = std::max(blo, a + 1); bb < bhi; ++bb)
                 if (orbN(a) + orbN(bb) <= limit)
-                    groups[{orbM(a) + orbM(bb), (orbN(a) + orbN(bb)) & 1}].push_back({a, bb});
+                    groups[(size_t)(orbM(a) + orbM(bb) + mspan) * 2 + ((orbN(a) + orbN(bb)) & 1)].push_back({a, bb});
         int64_t off = 0;
-        for (auto &kv : groups) {
+        for (auto &grp : groups) {
+            if (grp.empty()) continue;
             int g = (int)L.gsize.size();
-            int n = (int)kv.second.size();
+            int n = (int)grp.size();
             if (g >= (1 << 12) || n >= (1 << 16)) return fail(CIH_ERR_UNSUPPORTED, "table group too large");
             L.gsize.push_back(n);
             L.goff.push_back(base + off);
             for (int u = 0; u < n; ++u) {
-                int a = kv.second[u].first, bb = kv.second[u].second;
+                int a = grp[u].first, bb = grp[u].second;
                 L.pid[(size_t)a * ntot + bb] = pair_code(g, u, false);
                 L.pid[(size_t)bb * ntot + a] = pair_code(g, u, true);
             }
@@ -244,6 +305,7 @@ int build_host_basis(const cih_space_t &sp, cih_basis &b)
     if (sp.Z < 0 || sp.N < 0 || sp.Nmax < 0) return fail(CIH_ERR_ARG, "Z, N and Nmax must be >= 0");
     if (sp.Z > 64 || sp.N > 64) return fail(CIH_ERR_UNSUPPORTED, "more than 64 particles of a species");
     b.space = sp;
+    Timer tm("host basis");
     int Zs[2] = {sp.Z, sp.N};
     for (int t = 0; t < 2; ++t) {
         Species &s = b.s[t];
@@ -263,41 +325,47 @@ int build_host_basis(const cih_space_t &sp, cih_basis &b)
     for (int t = 0; t < 2; ++t) {
         Species &s = b.s[t];
         s.Nsub_max = b.Nlim - b.s[1 - t].N0;
-        Colex g(s);
-        g.rec(s.Z, s.n_orb, s.Nsub_max, 0, 0);
-        bucket_sort(s, g);
+        enumerate_subdets(s);
+        tm.mark(t == 0 ? "enumerate p" : "enumerate n");
         words = std::max(words, (s.n_orb + 63) / 64);
     }
     b.W = words <= 1 ? 1 : words <= 2 ? 2 : 4;
+    tm.mark("enumerate + bucket sort");
 
     // appearing sub-dets: x pairs with some y of the other species when the
     // lowest-N partner of the right (2M, parity) fits under Nlim
     for (int t = 0; t < 2; ++t) {
         const Species &o = b.s[1 - t];
-        std::map<std::pair<int, int>, int> minN;
-        for (int64_t i = 0; i < o.n_sd; ++i) {
-            auto k = std::make_pair(o.M2[i], o.N[i] & 1);
-            auto it = minN.find(k);
-            if (it == minN.end() || o.N[i] < it->second) minN[k] = o.N[i];
-        }
         Species &s = b.s[t];
+        int mspan = std::abs(sp.twoM);
+        for (int64_t i = 0; i < o.n_sd; ++i) mspan = std::max(mspan, std::abs(o.M2[i]));
+        for (int64_t i = 0; i < s.n_sd; ++i) mspan = std::max(mspan, std::abs(s.M2[i]) + std::abs(sp.twoM));
+        std::vector<int> minN((size_t)(2 * mspan + 1) * 2, INT_MAX);   // (2M + mspan) * 2 + parity
+        for (int64_t i = 0; i < o.n_sd; ++i) {
+            int &m = minN[(size_t)(o.M2[i] + mspan) * 2 + (o.N[i] & 1)];
+            m = std::min(m, o.N[i]);
+        }
         std::vector<char> keep(s.n_sd, 0);
         for (int64_t i = 0; i < s.n_sd; ++i) {
             int room = b.Nlim - s.N[i];
-            if (room < 0) continue;
-            auto it = minN.find({sp.twoM - s.M2[i], room & 1});
-            keep[i] = it != minN.end() && it->second <= room;
+            int mo = sp.twoM - s.M2[i];
+            if (room < 0 || mo < -mspan || mo > mspan) continue;
+            keep[i] = minN[(size_t)(mo + mspan) * 2 + (room & 1)] <= room;
         }
         keep_only(s, keep);
     }
     // the filter of the second species used the first one's filtered list;
     // pairing is symmetric, so the first species' list is still exact.
     for (int t = 0; t < 2; ++t) make_classes(b.s[t]);
+    tm.mark("appearing filter + classes");
 
     // partner ranges: class of (2M - 2M_p, parity of Nlim - N_p), prefix N <= Nlim - N_p
     const Species &P = b.s[0], &Q = b.s[1];
-    std::map<std::pair<int, int>, int> ncls;
-    for (size_t c = 0; c < Q.cls_begin.size(); ++c) ncls[{Q.cls_M2[c], Q.cls_par[c]}] = (int)c;
+    int qspan = std::abs(sp.twoM);
+    for (size_t c = 0; c < Q.cls_begin.size(); ++c) qspan = std::max(qspan, std::abs(Q.cls_M2[c]));
+    for (int64_t i = 0; i < P.n_sd; ++i) qspan = std::max(qspan, std::abs(P.M2[i]) + std::abs(sp.twoM));
+    std::vector<int> ncls((size_t)(2 * qspan + 1) * 2, -1);               // (2M + qspan) * 2 + parity
+    for (size_t c = 0; c < Q.cls_begin.size(); ++c) ncls[(size_t)(Q.cls_M2[c] + qspan) * 2 + Q.cls_par[c]] = (int)c;
     std::vector<std::vector<int>> cum(Q.cls_begin.size());
     for (size_t c = 0; c < Q.cls_begin.size(); ++c) {
         cum[c].assign(b.Nlim + 2, 0);
@@ -310,9 +378,9 @@ int build_host_basis(const cih_space_t &sp, cih_basis &b)
     int64_t dim = 0;
     for (int64_t p = 0; p < P.n_sd; ++p) {
         int room = b.Nlim - P.N[p];
-        auto it = ncls.find({sp.twoM - P.M2[p], room & 1});
-        if (room < 0 || it == ncls.end()) return fail(CIH_ERR_ARG, "internal: proton sub-det without partners");
-        int c = it->second;
+        const int mo = sp.twoM - P.M2[p];
+        const int c = (room < 0 || mo < -qspan || mo > qspan) ? -1 : ncls[(size_t)(mo + qspan) * 2 + (room & 1)];
+        if (c < 0) return fail(CIH_ERR_ARG, "internal: proton sub-det without partners");
         b.nb[p] = Q.cls_begin[c];
         b.nc[p] = cum[c][std::min(room, b.Nlim) + 1];
         b.rowbase[p] = dim;
@@ -321,9 +389,13 @@ int build_host_basis(const cih_space_t &sp, cih_basis &b)
     b.rowbase[P.n_sd] = dim;
     b.dim = dim;
     if (dim > INT32_MAX) return fail(CIH_ERR_UNSUPPORTED, "dimension above 2^31-1 (int32 columns)");
+    tm.mark("partner ranges");
     int rc = build_layout(b);
+    tm.mark("table layout");
     if (rc) return rc;
-    return build_pn_split(b);
+    rc = build_pn_split(b);
+    tm.mark("pn split");
+    return rc;
 }
 
 }  // namespace cih

@@ -1,6 +1,10 @@
 // The C ABI declared in include/cih.h: argument checks, error codes, and the
 // order of device steps.  No C++ exception crosses it.
 #include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -27,6 +31,55 @@ int cuda_fail(cudaError_t e, const char *what)
     return CIH_ERR_CUDA;
 }
 
+int device_pool(int device, cudaMemPool_t *pool)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (device < 0 || device >= 64) return fail(CIH_ERR_UNSUPPORTED, "device index above 63");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaError_t e = cudaMemPoolCreate(&pools[device], &props);
+        if (e != cudaSuccess) return cuda_fail(e, "memory pool");
+        uint64_t keep = UINT64_MAX;                 // keep freed blocks for the next basis
+        cudaMemPoolSetAttribute(pools[device], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    *pool = pools[device];
+    return CIH_OK;
+}
+
+static double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static bool timing_on()
+{
+    static const bool on = std::getenv("CIH_TIMING") != nullptr;
+    return on;
+}
+
+Timer::Timer(const char *w) : what(w), t0(now_ms()) {}
+Timer::~Timer() { mark("end"); }
+void Timer::mark_sync(const char *phase, cudaStream_t st)
+{
+    if (!timing_on()) return;
+    cudaStreamSynchronize(st);
+    mark(phase);
+}
+
+void Timer::mark(const char *phase)
+{
+    if (!timing_on()) return;
+    double t = now_ms();
+    std::fprintf(stderr, "[cih] %s: %s %.3f ms\n", what, phase, t - t0);
+    t0 = t;
+}
+
 static void release(cih_basis *b)
 {
     if (!b) return;
@@ -34,7 +87,11 @@ static void release(cih_basis *b)
     bool switched = false;
     if (!b->buffers.owned.empty() && cudaGetDevice(&cur) == cudaSuccess && cur != b->device)
         switched = cudaSetDevice(b->device) == cudaSuccess;
-    for (void *p : b->buffers.owned) cudaFree(p);
+    if (!b->buffers.owned.empty()) {
+        cudaDeviceSynchronize();                     // no kernel may still read the tables
+        for (void *p : b->buffers.owned) cudaFreeAsync(p, 0);
+        cudaStreamSynchronize(0);
+    }
     if (switched) cudaSetDevice(cur);
     delete b;
 }
@@ -76,7 +133,9 @@ int cih_basis_enumerate(const cih_space_t *space, cih_basis_h *out, void *stream
     *out = nullptr;
     return guarded([&]() -> int {
         cih_basis *b = new cih_basis;
+        Timer tm("basis");
         int rc = build_host_basis(*space, *b);
+        tm.mark("host tables");
         if (!rc) {
             cudaError_t e = cudaGetDevice(&b->device);
             rc = e == cudaSuccess ? upload_and_build_neighbours(*b, (cudaStream_t)stream)

@@ -101,6 +101,8 @@ struct SpeciesBuild {
     const int8_t *oN;           // per orbital
     const int16_t *om2;
     int32_t n_sd, n_orb, moff, mspan, Nsub_max;
+    const int32_t *hash;        // open-addressing table of sub-det indices, -1 = empty
+    uint32_t hash_mask;         // capacity - 1 (power of two)
 };
 
 // ---------------------------------------------------------------- host side
@@ -162,12 +164,27 @@ struct cih_basis {
     int64_t scan_scratch_len = 0;
     int *dev_status = nullptr;                // kernel error word
     int device = 0;
+    cudaMemPool_t pool = nullptr;             // library pool the handle's buffers come from
+    cudaStream_t stream = nullptr;            // stream of the build
 };
 
 namespace cih {
 
 // every kernel launch site adds the launches it makes (capi.cpp)
 void count_launches(int64_t n);
+
+// the library's device memory pool of a device (keeps freed memory for reuse)
+int device_pool(int device, cudaMemPool_t *pool);
+
+// phase timer printed to stderr when the environment sets CIH_TIMING
+struct Timer {
+    const char *what;
+    double t0;
+    explicit Timer(const char *w);
+    ~Timer();
+    void mark(const char *phase);
+    void mark_sync(const char *phase, cudaStream_t st);   // synchronises st only when timing is on
+};
 
 // error reporting (capi.cpp)
 int fail(int code, const std::string &msg);

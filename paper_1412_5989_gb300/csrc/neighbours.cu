@@ -63,9 +63,55 @@ __global__ void k_forward(SpeciesBuild S, int64_t *cnt, const int64_t *off, int3
     }
 }
 
-// index of the sub-det with bits `yb`, quanta Ny and 2M My, or -1
+template <int W>
+__device__ __forceinline__ uint32_t hash_bits(const uint64_t *b)
+{
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        h ^= b[w] + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
+        h *= 0xBF58476D1CE4E5B9ull;
+    }
+    return (uint32_t)(h ^ (h >> 31));
+}
+
+// insert every sub-det index (all keys distinct: claim the first empty slot)
+template <int W>
+__global__ void k_hash_build(SpeciesBuild S, int32_t *table)
+{
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < S.n_sd; x += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t h = hash_bits<W>(S.bits + x * W) & S.hash_mask;
+        for (uint32_t probe = 0; probe <= S.hash_mask; ++probe) {
+            if (atomicCAS(&table[h], -1, (int32_t)x) == -1) break;
+            h = (h + 1) & S.hash_mask;
+        }
+    }
+}
+
+// index of the sub-det with bits `yb`, or -1 (hash lookup; at most capacity probes)
 template <int W>
 __device__ int find_subdet(const SpeciesBuild &S, const uint64_t (&yb)[W], int Ny, int My)
+{
+    (void)Ny;
+    (void)My;
+    uint32_t h = hash_bits<W>(yb) & S.hash_mask;
+    for (uint32_t probe = 0; probe <= S.hash_mask; ++probe) {
+        const int32_t x = S.hash[h];
+        if (x < 0) return -1;
+        const uint64_t *xb = S.bits + (int64_t)x * W;
+        bool eq = true;
+#pragma unroll
+        for (int w = 0; w < W; ++w) eq &= xb[w] == yb[w];
+        if (eq) return x;
+        h = (h + 1) & S.hash_mask;
+    }
+    return -1;
+}
+
+// index of the sub-det with bits `yb`, quanta Ny and 2M My, or -1 (binary
+// search inside its class; kept for reference)
+template <int W>
+__device__ int find_subdet_sorted(const SpeciesBuild &S, const uint64_t (&yb)[W], int Ny, int My)
 {
     int key = My + S.moff;
     if (key < 0 || key >= S.mspan) return -1;
@@ -420,18 +466,159 @@ __global__ void k_row_p(int64_t np, const int64_t *rowbase, int32_t *row_p)
         for (int64_t r = rowbase[p] + lane; r < rowbase[p + 1]; r += 32) row_p[r] = (int32_t)p;
 }
 
+// Single-pass forward lists: sub-det x at rank r of a class [cb, ce) of size
+// m has room for m - r - 1 entries at stage offset
+//   class_stage[c] + r (m - 1) - r (r - 1) / 2,
+// written in ascending order; cnt[x] gets the count.
+template <int W>
+__global__ void k_forward_staged(SpeciesBuild S, const int32_t *cls_of, const int64_t *class_stage, int64_t *cnt,
+                                 int32_t *stage)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp; x < S.n_sd; x += nwarps) {
+        uint64_t bx[W];
+        load_bits<W>(S.bits, x, bx);
+        const int c = cls_of[x];
+        const int64_t cb = S.cls_begin[c], m = S.cls_endc[c] - cb, r = x - cb;
+        int32_t *out = stage + class_stage[c] + r * (m - 1) - r * (r - 1) / 2;
+        const int end = S.cls_end[x];
+        int64_t pos = 0;
+        for (int y0 = (int)x + 1; y0 < end; y0 += 32) {
+            const int y = y0 + lane;
+            bool hit = false;
+            if (y < end) hit = xor_pop<W>(bx, S.bits + (int64_t)y * W) <= 4;
+            const unsigned msk = __ballot_sync(0xffffffffu, hit);
+            if (hit) out[pos + __popc(msk & ((1u << lane) - 1))] = y;
+            pos += __popc(msk);
+        }
+        if (lane == 0) cnt[x] = pos;
+    }
+}
+
+__global__ void k_forward_compact(SpeciesBuild S, const int32_t *cls_of, const int64_t *class_stage,
+                                  const int64_t *off, const int32_t *stage, int32_t *out)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp; x < S.n_sd; x += nwarps) {
+        const int c = cls_of[x];
+        const int64_t cb = S.cls_begin[c], m = S.cls_endc[c] - cb, r = x - cb;
+        const int32_t *in = stage + class_stage[c] + r * (m - 1) - r * (r - 1) / 2;
+        const int64_t o = off[x], len = off[x + 1] - o;
+        for (int64_t i = lane; i < len; i += 32) out[o + i] = in[i];
+    }
+}
+
+// Single-pass one-move lists: each sub-det writes its moves (unsorted) into
+// a slot of `cap` entries; cnt[x] gets the count.
+template <int W>
+__global__ void k_onemove_staged(SpeciesBuild S, int cap, int64_t *cnt, int32_t *stage)
+{
+    int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp; x < S.n_sd; x += nwarps) {
+        uint64_t bx[W];
+        load_bits<W>(S.bits, x, bx);
+        const int Nx = S.N[x];
+        int32_t *out = stage + x * (int64_t)cap;
+        int pos = 0;
+        for (int w = 0; w < W; ++w) {
+            uint64_t occ = bx[w];
+            while (occ) {
+                const int r = w * 64 + __ffsll((long long)occ) - 1;
+                occ &= occ - 1;
+                const int Nr = S.oN[r];
+                for (int a0 = 0; a0 < S.n_orb; a0 += 32) {
+                    const int a = a0 + lane;
+                    int found = -1;
+                    if (a < S.n_orb && !((bx[a >> 6] >> (a & 63)) & 1) && Nx - Nr + S.oN[a] <= S.Nsub_max) {
+                        uint64_t yb[W];
+#pragma unroll
+                        for (int v = 0; v < W; ++v) yb[v] = bx[v];
+                        yb[r >> 6] &= ~(1ull << (r & 63));
+                        yb[a >> 6] |= 1ull << (a & 63);
+                        found = find_subdet<W>(S, yb, 0, 0);
+                    }
+                    const unsigned msk = __ballot_sync(0xffffffffu, found >= 0);
+                    if (found >= 0) out[pos + __popc(msk & ((1u << lane) - 1))] = found;
+                    pos += __popc(msk);
+                }
+            }
+        }
+        if (lane == 0) cnt[x] = pos;
+    }
+}
+
+// one block per list: bitonic sort of the staged moves in shared memory,
+// written compact at off[x]
+__global__ void k_onemove_compact_sort(int64_t n, int cap, const int64_t *off, const int32_t *stage, int32_t *out)
+{
+    __shared__ int32_t sh[kSortTile];
+    for (int64_t x = blockIdx.x; x < n; x += gridDim.x) {
+        const int64_t o = off[x];
+        const int len = (int)(off[x + 1] - o);
+        const int32_t *in = stage + x * (int64_t)cap;
+        if (len <= 32) {                          // small lists: one warp, insertion by rank
+            if (threadIdx.x < 32) {
+                const int32_t v = threadIdx.x < len ? in[threadIdx.x] : INT32_MAX;
+                int rank = 0;
+                for (int j = 0; j < len; ++j) {
+                    const int32_t u = __shfl_sync(0xffffffffu, v, j);
+                    rank += (u < v);
+                }
+                if ((int)threadIdx.x < len) out[o + rank] = v;
+            }
+            continue;
+        }
+        int P = 1;
+        while (P < len) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < len ? in[i] : INT32_MAX;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const bool up = (i & k) == 0;
+                        const int32_t a = sh[i], c = sh[l];
+                        if ((a > c) == up) { sh[i] = c; sh[l] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < len; i += blockDim.x) out[o + i] = sh[i];
+        __syncthreads();
+    }
+}
+
 template <class T>
 int dev_alloc(cih_basis &b, T **p, size_t n)
 {
     *p = nullptr;
-    size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc((void **)p, bytes);
+    size_t bytes = (std::max<size_t>(n, 1) * sizeof(T) + 255) / 256 * 256;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)p, bytes, b.pool, b.stream);
     if (e != cudaSuccess) {
         *p = nullptr;
-        return fail(CIH_ERR_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        (void)cudaGetLastError();
+        return fail(CIH_ERR_NOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
     }
     b.buffers.owned.push_back((void *)*p);
     return CIH_OK;
+}
+
+// return a buffer to the pool once the stream has passed its last use
+template <class T>
+void dev_free(cih_basis &b, T *p)
+{
+    if (!p) return;
+    auto &v = b.buffers.owned;
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i] == (void *)p) { v.erase(v.begin() + i); break; }
+    cudaFreeAsync((void *)p, b.stream);
 }
 
 template <class T>
@@ -458,18 +645,39 @@ int grid_for(int64_t warps)
 template <int W>
 int build_lists(cih_basis &b, int t, SpeciesBuild &S, cudaStream_t st)
 {
+    Timer tm(t == 0 ? "lists p" : "lists n");
     DevSpecies &D = b.dev.sp[t];
-    int64_t n = S.n_sd;
+    const Species &hs = b.s[t];
+    const int64_t n = S.n_sd;
     int64_t *cnt_fw, *cnt_n1, *scratch;
     int rc;
     if ((rc = dev_alloc(b, &cnt_fw, n + 1)) || (rc = dev_alloc(b, &cnt_n1, n + 1))) return rc;
-    int64_t ns = scan_scratch_needed(n);
+    const int64_t ns = scan_scratch_needed(n);
     if ((rc = dev_alloc(b, &scratch, ns))) return rc;
-    int grid = grid_for(n);
+    const int grid = grid_for(n);
+    // staging: forward lists by class triangle, one-move lists by fixed slots
+    std::vector<int32_t> cls_of(std::max<int64_t>(n, 1));
+    std::vector<int64_t> class_stage(std::max<size_t>(hs.cls_begin.size(), 1));
+    int64_t fw_stage = 0;
+    for (size_t c = 0; c < hs.cls_begin.size(); ++c) {
+        const int64_t m = hs.cls_end[c] - hs.cls_begin[c];
+        class_stage[c] = fw_stage;
+        fw_stage += m * (m - 1) / 2;
+        for (int64_t x = hs.cls_begin[c]; x < hs.cls_end[c]; ++x) cls_of[x] = (int32_t)c;
+    }
+    const int cap1 = std::max(1, hs.Z * std::max(0, hs.n_orb - hs.Z));
+    if (cap1 > kSortTile) return fail(CIH_ERR_UNSUPPORTED, "one-move lists longer than the sort tile");
+    int32_t *d_cls_of, *fw_st, *n1_st;
+    int64_t *d_class_stage;
+    if ((rc = upload(b, &d_cls_of, cls_of, st)) || (rc = upload(b, &d_class_stage, class_stage, st)) ||
+        (rc = dev_alloc(b, &fw_st, fw_stage)) || (rc = dev_alloc(b, &n1_st, (size_t)n * cap1)))
+        return rc;
     if (n > 0) {
         count_launches(2);
-        k_forward<W, false><<<grid, 256, 0, st>>>(S, cnt_fw, nullptr, nullptr);
-        k_onemove<W, false><<<grid, 256, 0, st>>>(S, cnt_n1, nullptr, nullptr);
+        k_forward_staged<W><<<grid, 256, 0, st>>>(S, d_cls_of, d_class_stage, cnt_fw, fw_st);
+        tm.mark_sync("forward pass", st);
+        k_onemove_staged<W><<<grid, 256, 0, st>>>(S, cap1, cnt_n1, n1_st);
+        tm.mark_sync("one-move pass", st);
     }
     if ((rc = exclusive_scan_i64(cnt_fw, n, scratch, ns, st))) return rc;
     if ((rc = exclusive_scan_i64(cnt_n1, n, scratch, ns, st))) return rc;
@@ -478,22 +686,17 @@ int build_lists(cih_basis &b, int t, SpeciesBuild &S, cudaStream_t st)
     cudaMemcpyAsync(&tot[1], cnt_n1 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "neighbour count");
+    tm.mark("scan");
     int32_t *fw, *n1;
     if ((rc = dev_alloc(b, &fw, tot[0])) || (rc = dev_alloc(b, &n1, tot[1]))) return rc;
     if (n > 0) {
         count_launches(2);
-        k_forward<W, true><<<grid, 256, 0, st>>>(S, nullptr, cnt_fw, fw);
-        k_onemove<W, true><<<grid, 256, 0, st>>>(S, nullptr, cnt_n1, n1);
+        k_forward_compact<<<grid, 256, 0, st>>>(S, d_cls_of, d_class_stage, cnt_fw, fw_st, fw);
+        k_onemove_compact_sort<<<(int)std::min<int64_t>(n, 65535), 256, 0, st>>>(n, cap1, cnt_n1, n1_st, n1);
     }
-    // the sort tile bounds the one-move list length: check it on the host
-    std::vector<int64_t> hoff(n + 1);
-    e = cudaMemcpyAsync(hoff.data(), cnt_n1, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "neighbour offsets");
-    for (int64_t x = 0; x < n; ++x)
-        if (hoff[x + 1] - hoff[x] > kSortTile) return fail(CIH_ERR_UNSUPPORTED, "one-move list longer than the sort tile");
-    if (n > 0) count_launches(1);
-    if (n > 0) k_sort_lists<<<(int)std::min<int64_t>(n, 65535), 256, 0, st>>>(cnt_n1, n1, n);
+    tm.mark_sync("compact + sort", st);
+    dev_free(b, fw_st);
+    dev_free(b, n1_st);
     int64_t *later;
     int *dmax;
     if ((rc = dev_alloc(b, &later, n)) || (rc = dev_alloc(b, &dmax, 1))) return rc;
@@ -519,6 +722,7 @@ int build_lists(cih_basis &b, int t, SpeciesBuild &S, cudaStream_t st)
         }
         b.dev.n1_info = info;
     }
+    tm.mark_sync("sort + later + two-move + info", st);
     int mc = 0;
     e = cudaMemcpyAsync(&mc, dmax, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -540,6 +744,9 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
 {
     int rc;
     int W = b.W;
+    b.stream = st;
+    if ((rc = device_pool(b.device, &b.pool))) return rc;
+    Timer tm("basis device set-up");
     if ((rc = dev_alloc(b, &b.dev_status, 4))) return rc;
     b.dev.queue = b.dev_status + 1;
     if (cudaMemsetAsync(b.dev_status, 0, 4 * sizeof(int), st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "status");
@@ -566,6 +773,7 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
     b.dev.ntot = ntot;
     b.dev.dim = b.dim;
     b.dev.tbme_len = b.layout.total;
+    tm.mark_sync("basis tables upload", st);
     {
         std::vector<int8_t> m2p(std::max(b.s[0].n_orb, 1), 0), Np(std::max(b.s[0].n_orb, 1), 0);
         for (int a = 0; a < b.s[0].n_orb; ++a) { m2p[a] = (int8_t)b.s[0].om2[a]; Np[a] = (int8_t)b.s[0].oN[a]; }
@@ -598,6 +806,7 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
         std::vector<int32_t> cb(s.cls_begin.begin(), s.cls_begin.end()), ce(s.cls_end.begin(), s.cls_end.end());
         std::vector<int8_t> oN(s.oN.begin(), s.oN.end());
         std::vector<int16_t> om2(s.om2.begin(), s.om2.end());
+        tm.mark_sync(t == 0 ? "species p host prep" : "species n host prep", st);
 
         uint64_t *d_bits; int8_t *d_N; int16_t *d_M2; int32_t *d_cls_end, *d_lookup, *d_cb, *d_ce;
         int8_t *d_oN; int16_t *d_om2;
@@ -616,15 +825,33 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
         D.orb_base = t == 0 ? 0 : b.s[0].n_orb;
 
         SpeciesBuild S{d_bits, d_N, d_M2, d_cls_end, d_lookup, d_cb, d_ce, d_oN, d_om2,
-                       (int32_t)s.n_sd, s.n_orb, moff, mspan, s.Nsub_max};
+                       (int32_t)s.n_sd, s.n_orb, moff, mspan, s.Nsub_max, nullptr, 0};
+        {
+            uint32_t cap = 64;
+            while (cap < 2 * (uint64_t)s.n_sd) cap <<= 1;
+            int32_t *table;
+            if ((rc = dev_alloc(b, &table, cap))) return rc;
+            if (cudaMemsetAsync(table, 0xFF, sizeof(int32_t) * cap, st) != cudaSuccess)
+                return cuda_fail(cudaGetLastError(), "hash table");
+            S.hash = table;
+            S.hash_mask = cap - 1;
+            const int hg = (int)std::min<int64_t>((s.n_sd + 255) / 256 + 1, 65535);
+            count_launches(1);
+            if (W == 1) k_hash_build<1><<<hg, 256, 0, st>>>(S, table);
+            else if (W == 2) k_hash_build<2><<<hg, 256, 0, st>>>(S, table);
+            else k_hash_build<4><<<hg, 256, 0, st>>>(S, table);
+        }
         b.sbuild[t] = S;
+        tm.mark_sync(t == 0 ? "species p upload" : "species n upload", st);
         if (W == 1) rc = build_lists<1>(b, t, S, st);
         else if (W == 2) rc = build_lists<2>(b, t, S, st);
         else rc = build_lists<4>(b, t, S, st);
         if (rc) return rc;
+        tm.mark_sync(t == 0 ? "species p lists" : "species n lists", st);
     }
     b.scan_scratch_len = scan_scratch_needed(b.dim);
     if ((rc = dev_alloc(b, &b.scan_scratch, b.scan_scratch_len))) return rc;
+    tm.mark_sync("scratch", st);
     {
         // neutron one-move lists: packed entries and bucket directory
         const Species &Q = b.s[1];
@@ -666,6 +893,7 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
             k_occ<4><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
             k_occ<4><<<g1, 256, 0, st>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
         }
+        tm.mark_sync("directory + occupied lists", st);
         b.dev.self_rel = srel;
         b.dev.occ[0] = occp;
         b.dev.occ[1] = occn;
@@ -701,6 +929,7 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
             else k_cand<4><<<grid, 256, 0, st>>>(SB, b.dev, SB.N, SB.M2, b.Nlim, coff, cand, cself);
             k_row_p<<<grid, 256, 0, st>>>(np, b.dev.rowbase, row_p);
         }
+        tm.mark_sync("candidate table", st);
         b.dev.cand_off = coff;
         b.dev.cand = cand;
         b.dev.cand_self = cself;
