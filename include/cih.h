@@ -179,6 +179,30 @@ int cih_check(cih_basis_h h, void *stream);
  * holds eigenvector k in column k.  Errors: CIH_ERR_ARG, CIH_ERR_NOMEM. */
 int cih_tridiag_eigen(int32_t n, const double *diag, const double *offdiag, double *evals, double *evecs);
 
+/* Row-pointer scan that makes no device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate GPU
+ * memory -- for example code that must run inside a framework whose memory
+ * is all held by that framework's own pool, or a serving path that has
+ * reserved its memory up front and may not call cudaMalloc (which can also
+ * block the whole device) once it is running.
+ *
+ * Writes the exclusive prefix sum of counts_dev[0..n) into rowptr_dev[0..n]
+ * (rowptr[0] = 0, rowptr[n] = total), the same result as the scan inside
+ * cih_ham_count.  Both arrays are device memory owned by the caller;
+ * counts_dev may equal rowptr_dev (scan in place).  Stream-ordered on
+ * `stream`; does not synchronise.
+ *
+ * Scratch: the block sums live in a fixed 128 KiB array inside the library
+ * (16,384 int64), which every GPU that loads the library holds until the
+ * process exits.  Hence n is limited to 67,108,864 (16,384 tiles of 4,096
+ * rows); larger n returns CIH_ERR_CAPACITY.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array: calls whose work can overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.
+ * Errors: CIH_ERR_ARG, CIH_ERR_CAPACITY, CIH_ERR_CUDA. */
+int cih_rowptr_scan_static(const int64_t *counts_dev, int64_t n, int64_t *rowptr_dev, void *stream);
+
 /* Number of kernels this library has launched in the process so far (all
  * devices, all handles): the difference across a region counts the region's
  * launches.  Errors: CIH_ERR_ARG. */

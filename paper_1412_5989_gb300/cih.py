@@ -44,6 +44,7 @@ _SIGS = {
     "cih_ham_tbme_grad": [_P, _P, C.c_int32, _P, _P, _P],
     "cih_tridiag_eigen": [C.c_int32, _dp, _dp, _dp, _dp],
     "cih_kernel_launches": [_i64p],
+    "cih_rowptr_scan_static": [_P, C.c_int64, _P, _P],
     "cih_strerror": [C.c_int],
     "cih_last_error_detail": [],
 }
@@ -90,6 +91,20 @@ def kernel_launches() -> int:
     n = C.c_int64()
     _ok(lib.cih_kernel_launches(C.byref(n)), "kernel_launches")
     return n.value
+
+
+def rowptr_scan_static(counts, rowptr=None, stream=None):
+    """Row pointers from per-row counts with the scan that allocates no device
+    memory (cih_rowptr_scan_static).  counts: int64 CUDA tensor (n,); returns
+    (or fills) an int64 CUDA tensor (n + 1,)."""
+    import torch
+    n = counts.numel()
+    if counts.dtype != torch.int64 or not counts.is_cuda or not counts.is_contiguous():
+        raise ValueError("counts must be a contiguous int64 CUDA tensor")
+    if rowptr is None:
+        rowptr = torch.empty(n + 1, dtype=torch.int64, device=counts.device)
+    _ok(lib.cih_rowptr_scan_static(_ptr(counts), n, _ptr(rowptr), _stream(stream)), "rowptr_scan_static")
+    return rowptr
 
 
 def tridiag_eigen(diag, offdiag):

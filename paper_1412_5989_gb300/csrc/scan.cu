@@ -1,6 +1,8 @@
 // Exclusive prefix sum over int64 counts (the "count" half of Sec. 4.1's two
 // passes turned into row pointers).  Three deterministic phases: per-tile
 // sums, one block scanning the tile sums, per-tile scan plus carry-in.
+#include <mutex>
+
 #include "cih_internal.h"
 
 namespace cih {
@@ -127,4 +129,57 @@ int exclusive_scan_i64(int64_t *data, int64_t n, int64_t *block_sums, int64_t bl
     return CIH_OK;
 }
 
+// ---------------------------------------------------------------- no-allocation variant
+//
+// The same scan with its tile sums in a fixed device array that lives in this
+// library's module instead of caller or library allocations.  Every call on a
+// device uses the same array; phase 1 rewrites every tile sum the call reads, so
+// nothing has to be cleared between calls, but two calls whose work overlaps on
+// the GPU (different streams, or host threads) race on it.
+
+namespace {
+
+constexpr int64_t kStaticTileSums = 16384;                 // 128 KiB on every device that loads the library
+static __device__ __align__(256) int64_t g_static_tile_sums[kStaticTileSums];
+
+// device address of the array, resolved once per device with that device current
+int static_tile_sums(int device, int64_t **out)
+{
+    static std::mutex mu;
+    static int64_t *addr[64] = {};
+    if (device < 0 || device >= 64) return fail(CIH_ERR_UNSUPPORTED, "device index above 63");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_tile_sums);
+        if (e != cudaSuccess) return cuda_fail(e, "static scan scratch: cudaGetSymbolAddress");
+        addr[device] = (int64_t *)p;
+    }
+    *out = addr[device];
+    return CIH_OK;
+}
+
+}  // namespace
+
 }  // namespace cih
+
+extern "C" int cih_rowptr_scan_static(const int64_t *counts_dev, int64_t n, int64_t *rowptr_dev, void *stream)
+{
+    using namespace cih;
+    if (n < 0 || !rowptr_dev || (n > 0 && !counts_dev)) return fail(CIH_ERR_ARG, "NULL array or negative length");
+    if (n > kStaticTileSums * kScanTile)
+        return fail(CIH_ERR_CAPACITY, "rowptr_scan_static: more than 67108864 rows (16384 tiles of 4096)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    int64_t *sums = nullptr;
+    int rc = static_tile_sums(dev, &sums);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n > 0 && counts_dev != rowptr_dev) {
+        e = cudaMemcpyAsync(rowptr_dev, counts_dev, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "rowptr_scan_static: copy counts");
+    }
+    return exclusive_scan_i64(rowptr_dev, n, sums, kStaticTileSums, st);
+}
+
