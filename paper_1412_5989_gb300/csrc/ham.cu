@@ -350,10 +350,11 @@ constexpr int pi = goff + kGroupCap * 4;                   // uint8[kPairCap]
 constexpr int pj = pi + kPairCap;                          // uint8[kPairCap]
 constexpr int warp0 = (pj + kPairCap + 15) / 16 * 16;
 // per warp
-constexpr int w_seg = 0;                                   // int4[32]: colbase, uv, mv, aux
-constexpr int w_incl = w_seg + 32 * 16;                    // int32[32]
-constexpr int w_n1s = w_incl + 128;                        // int32[32]
-constexpr int w_spos = w_n1s + 128;                       // int32[kSlowCap]
+constexpr int w_seg = 0;                                   // int4[64]: colbase, uv, mv, row start
+constexpr int w_incl = w_seg + 64 * 16;                    // int32[64]
+constexpr int w_n1s = w_incl + 256;                        // int32[64]
+constexpr int w_ins = w_n1s + 256;                         // int32[64]
+constexpr int w_spos = w_ins + 256;                       // int32[kSlowCap]
 constexpr int w_scol = w_spos + kSlowCap * 4;              // int32[kSlowCap]
 constexpr int w_scode = w_scol + kSlowCap * 4;             // uint32[kSlowCap]
 constexpr int w_occ = w_scode + kSlowCap * 4;              // int16[kMaxA]
@@ -509,6 +510,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     unsigned char *wb = sb + sm::warp0 + wid * sm::w_size;
     int4 *w_seg = sptr<int4>(wb, sm::w_seg);
     int32_t *w_incl = sptr<int32_t>(wb, sm::w_incl), *w_n1s = sptr<int32_t>(wb, sm::w_n1s);
+    int32_t *w_ins = sptr<int32_t>(wb, sm::w_ins);
     int32_t *w_spos = sptr<int32_t>(wb, sm::w_spos), *w_scol = sptr<int32_t>(wb, sm::w_scol);
     uint32_t *w_scode = sptr<uint32_t>(wb, sm::w_scode);
     int16_t *w_occ = sptr<int16_t>(wb, sm::w_occ);
@@ -605,33 +607,34 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
             }
         }
 
-        // ---- B: candidates of p in chunks of 32 (records of the next chunk
-        //      are loaded while the current one is emitted)
+        // ---- B: candidates of p in chunks of 64, two per lane (records of the
+        //      next chunk are loaded while the current one is emitted)
         const int64_t c0 = B.cand_off[p], c1 = B.cand_off[p + 1];
-        const int64_t n1a = SN.n1_off[n];
+        const int2 *n1row = B.n1p + SN.n1_off[n];
         const int16_t *dirn = B.dir + (int64_t)n * B.dir_len;
         const int Nn = SN.N[n];
         const int self_rel = B.self_rel[n];
-        int4 rn_ = make_int4(0, 0, 0, 0);
-        int sln = 0;
-        if (c0 + lane < c1) { rn_ = B.cand[c0 + lane]; sln = B.cand_self[c0 + lane]; }
-        for (int64_t k0 = c0; k0 < c1; k0 += 32) {
-            const bool valid = k0 + lane < c1;
-            const int4 r = rn_;
-            const int sl = valid ? sln : 0;
-            if (k0 + 32 + lane < c1) { rn_ = B.cand[k0 + 32 + lane]; sln = B.cand_self[k0 + 32 + lane]; }
-            // this lane's candidate: pn neutron moves [s_rel, s_rel + lpn) of n's list,
+        int4 rn0 = make_int4(0, 0, 0, 0), rn1 = rn0;
+        int sln0 = 0, sln1 = 0;
+        if (c0 + 2 * lane < c1) { rn0 = B.cand[c0 + 2 * lane]; sln0 = B.cand_self[c0 + 2 * lane]; }
+        if (c0 + 2 * lane + 1 < c1) { rn1 = B.cand[c0 + 2 * lane + 1]; sln1 = B.cand_self[c0 + 2 * lane + 1]; }
+        for (int64_t k0 = c0; k0 < c1; k0 += 64) {
+            const int4 r0 = rn0, r1 = rn1;
+            const int sl0 = k0 + 2 * lane < c1 ? sln0 : 0, sl1 = k0 + 2 * lane + 1 < c1 ? sln1 : 0;
+            const bool v0 = k0 + 2 * lane < c1, v1 = k0 + 2 * lane + 1 < c1;
+            if (k0 + 64 + 2 * lane < c1) { rn0 = B.cand[k0 + 64 + 2 * lane]; sln0 = B.cand_self[k0 + 64 + 2 * lane]; }
+            if (k0 + 65 + 2 * lane < c1) { rn1 = B.cand[k0 + 65 + 2 * lane]; sln1 = B.cand_self[k0 + 65 + 2 * lane]; }
+            // each candidate: pn neutron moves [s_rel, s_rel + lpn) of n's list,
             // plus n itself (a pp two-move or a one-proton move) if inside q's range
-            const bool self = (sl & 0x7F) > Nn;                    // 1 + L_q > N_n
-            const int two = sl >> 7;
-            int lpn = 0, s_rel = 0;
-            if (valid && !two) {
-                s_rel = dirn[r.y & 0xFFFF];
-                lpn = dirn[(unsigned)r.y >> 16] - s_rel;
-            }
-            const int ltot = lpn + (self ? 1 : 0);
-            // one scan of both counts: pn elements in the low half, all in the high half
-            int incl = lpn | (ltot << 16);
+            const bool self0 = (sl0 & 0x7F) > Nn, self1 = (sl1 & 0x7F) > Nn;   // 1 + L_q > N_n
+            const int two0 = sl0 >> 7, two1 = sl1 >> 7;
+            int lpn0 = 0, s0 = 0, lpn1 = 0, s1 = 0;
+            if (v0 && !two0) { s0 = dirn[r0.y & 0xFFFF]; lpn0 = dirn[(unsigned)r0.y >> 16] - s0; }
+            if (v1 && !two1) { s1 = dirn[r1.y & 0xFFFF]; lpn1 = dirn[(unsigned)r1.y >> 16] - s1; }
+            const int lt0 = lpn0 + (self0 ? 1 : 0), lt1 = lpn1 + (self1 ? 1 : 0);
+            // one scan of both counts (pn elements low half, all elements high half)
+            const int pair = (lpn0 + lpn1) | ((lt0 + lt1) << 16);
+            int incl = pair;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const int o2 = __shfl_up_sync(0xffffffffu, incl, d);
@@ -641,28 +644,47 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
             const int T = tot >> 16, Tpn = tot & 0xFFFF;
             if (MODE != 0 && T > 0) {
                 if (MODE == 1 && pos + T > rowlen) { atomicOr(status, 2); pos += T; continue; }
-                const int ex_all = pos + (incl >> 16) - ltot;           // row position of the segment
-                const int ins = self && !two ? self_rel - s_rel : -1;    // where n sorts among the pn moves
-                // n itself: written by its candidate's lane
-                if (self && two) {
-                    put_single<MODE, K1>(B, F, Gr, R, ex_all, (int64_t)r.x + n, (int)((uint32_t)r.z >> 1), r.z & 1);
-                }
-                const bool p1 = self && !two;
-                const unsigned smk = __ballot_sync(0xffffffffu, p1);
-                if (nslow + __popc(smk) > kSlowCap)
+                const int ex0 = pos + (incl >> 16) - (lt0 + lt1);        // row position of candidate 0
+                const int ex1 = ex0 + lt0;
+                const int ins0 = self0 && !two0 ? self_rel - s0 : -1;     // where n sorts among the pn moves
+                const int ins1 = self1 && !two1 ? self_rel - s1 : -1;
+                // n itself: written (pp two-move) or deferred (one-proton move) by its candidate's lane
+                if (self0 && two0)
+                    put_single<MODE, K1>(B, F, Gr, R, ex0, (int64_t)r0.x + n, (int)((uint32_t)r0.z >> 1), r0.z & 1);
+                if (self1 && two1)
+                    put_single<MODE, K1>(B, F, Gr, R, ex1, (int64_t)r1.x + n, (int)((uint32_t)r1.z >> 1), r1.z & 1);
+                const bool p0 = self0 && !two0, p1 = self1 && !two1;
+                const unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
+                if (nslow + __popc(m0) + __popc(m1) > kSlowCap)
                     flush_slow<MODE, K1>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
-                if (p1) {
-                    const int q = nslow + __popc(smk & lt);
-                    const uint32_t mv = (uint32_t)r.w;
-                    w_spos[q] = ex_all + ins;
-                    w_scol[q] = (int32_t)((int64_t)r.x + n);
+                if (p0) {
+                    const int q = nslow + __popc(m0 & lt);
+                    const uint32_t mv = (uint32_t)r0.w;
+                    w_spos[q] = ex0 + ins0;
+                    w_scol[q] = r0.x + n;
                     w_scode[q] = ((mv >> 16) & 0xFF) | (((mv >> 24) & 0xFF) << 8) | (((mv >> 9) & 1) << 16);
                 }
-                nslow += __popc(smk);
+                nslow += __popc(m0);
+                if (p1) {
+                    const int q = nslow + __popc(m1 & lt);
+                    const uint32_t mv = (uint32_t)r1.w;
+                    w_spos[q] = ex1 + ins1;
+                    w_scol[q] = r1.x + n;
+                    w_scode[q] = ((mv >> 16) & 0xFF) | (((mv >> 24) & 0xFF) << 8) | (((mv >> 9) & 1) << 16);
+                }
+                nslow += __popc(m1);
                 if (Tpn > 0) {
-                    w_incl[lane] = incl & 0xFFFF;
-                    w_seg[lane] = make_int4(r.x, r.z, r.w, ex_all);
-                    w_n1s[lane] = s_rel | ((ins + 1) << 16);      // both below 2^15 (sort tile)
+                    // segment table of the 64 candidates: inclusive pn counts, record, list start,
+                    // row start, insertion threshold (INT_MAX if n is not in the range)
+                    const int incl_pn = incl & 0xFFFF;
+                    w_incl[2 * lane] = incl_pn - lpn1;
+                    w_incl[2 * lane + 1] = incl_pn;
+                    w_seg[2 * lane] = make_int4(r0.x, r0.z, r0.w, ex0);
+                    w_seg[2 * lane + 1] = make_int4(r1.x, r1.z, r1.w, ex1);
+                    w_n1s[2 * lane] = s0;
+                    w_n1s[2 * lane + 1] = s1;
+                    w_ins[2 * lane] = ins0 >= 0 ? ins0 : INT32_MAX;
+                    w_ins[2 * lane + 1] = ins1 >= 0 ? ins1 : INT32_MAX;
                     __syncwarp();
                     const int iters = (Tpn + 31) >> 5;
                     for (int it = 0; it < iters; ++it) {
@@ -670,17 +692,15 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                         if (e < Tpn) {
                             int j = 0;
 #pragma unroll
-                            for (int step = 16; step > 0; step >>= 1)
+                            for (int step = 32; step > 0; step >>= 1)
                                 if (w_incl[j + step - 1] <= e) j += step;
                             const int tt = e - (j ? w_incl[j - 1] : 0);
                             const int4 sg4 = w_seg[j];
-                            const int nsj = w_n1s[j];
-                            const int insj = (nsj >> 16) - 1;
-                            const int at = sg4.w + tt + ((insj >= 0 && tt >= insj) ? 1 : 0);
-                            const int2 ent = B.n1p[n1a + (nsj & 0xFFFF) + tt];
+                            const int at = sg4.w + tt + (tt >= w_ins[j] ? 1 : 0);
+                            const int2 ent = n1row[w_n1s[j] + tt];
                             int sg;
                             const int idx = pn_index(sb, (uint32_t)sg4.y, (uint32_t)sg4.z, (uint32_t)ent.y, sg);
-                            put_single<MODE, K1>(B, F, Gr, R, at, (int64_t)sg4.x + ent.x, idx, sg);
+                            put_single<MODE, K1>(B, F, Gr, R, at, (int64_t)(sg4.x + ent.x), idx, sg);
                         }
                     }
                     __syncwarp();
