@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--workload", default="4p4n_nmax6", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=3000, help="rows in the oracle's timed sample")
+    ap.add_argument("--cpu-rows", type=int, default=60000, help="rows in the oracle's timed sample")
     return ap.parse_args()
 
 
@@ -325,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "kernel": "k_walk<4,1> (fill)", "algorithmic_bytes_per_launch": nnz * BYTES_PER_NNZ,
+                "kernel": "k_rows<4,1,K1> (fill)", "algorithmic_bytes_per_launch": nnz * BYTES_PER_NNZ,
                 "traffic": fill_traffic(kernel_source_sha())}
 
     cpu = None

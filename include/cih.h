@@ -140,17 +140,53 @@ int cih_ham_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hba
                  const float *tbme_dev, const double *e_sp_dev,
                  int32_t *col_dev, float *val_dev, void *stream);
 
+/* As cih_ham_fill, with the K tables interleaved element-major
+ * (tbme_il_dev[t * K + k] = entry t of set k; see cih_tbme_interleave), so that
+ * the K values of one nonzero come from one contiguous read.  Output layout as
+ * cih_ham_fill (values set-major).  Errors as cih_ham_fill. */
+int cih_ham_fill_interleaved(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,
+                             const float *tbme_il_dev, const double *e_sp_dev,
+                             int32_t *col_dev, float *val_dev, void *stream);
+
+/* tbme_il_dev[t * K + k] = tbme_dev[k * tbme_len + t] (device arrays, caller-
+ * owned, stream-ordered).  Errors: CIH_ERR_ARG, CIH_ERR_CUDA. */
+int cih_tbme_interleave(int32_t K, int64_t tbme_len, const float *tbme_dev, float *tbme_il_dev, void *stream);
+
+/* Launch shape of the row kernels (count, fill, adjoint) of this handle:
+ * warps_per_cta 8 or 16, ctas_per_sm 0 (as many as fit) or a cap.
+ * Errors: CIH_ERR_ARG. */
+int cih_set_launch(cih_basis_h h, int32_t warps_per_cta, int32_t ctas_per_sm);
+
+/* Autotuner: times the fill (cih_ham_fill, or cih_ham_fill_interleaved when
+ * interleaved != 0, same arguments) for every launch shape -- warps per CTA in
+ * {16, 8} x CTAs per SM in {as many as fit, 1, 2, 3} -- with CUDA events
+ * (best of two after one warm-up), keeps the fastest on the handle and reports
+ * it.  The outputs col_dev / val_dev are written (with the final, correct
+ * values).  Synchronises `stream`.  Errors as cih_ham_fill. */
+int cih_autotune_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,
+                      const float *tbme_dev, int32_t interleaved, const double *e_sp_dev,
+                      int32_t *col_dev, float *val_dev, void *stream,
+                      int32_t *best_warps, int32_t *best_ctas, float *best_ms);
+
 /* Lowest eigenpairs by Lanczos (Sec. 2) for each of K matrices sharing one
- * structure: FP32 half-stored values, FP64 matrix-vector accumulation, FP64
- * full reorthogonalisation, FP64 tridiagonal eigensolve on the host.
- *   val_dev: K x nnz float; nev: eigenvalues wanted (<= 64); max_iter:
- *   Lanczos steps (<= 2048); tol: relative residual bound on the nev Ritz
- *   pairs; evals_host: K x nev double (host, ascending; NaN where fewer
- *   converged Ritz values exist); evec0_dev: NULL or K x dim double (device),
- *   the normalised lowest Ritz vector of each set.
- * Lanczos vectors (max_iter x dim double per set) are library-allocated for
- * the duration of the call.  Returns 0, or 1 if some set did not meet tol
- * within max_iter (results still written), or a CIH_ERR_* code. */
+ * structure (the output of one cih_ham_fill call): FP32 half-stored values,
+ * FP64 vectors and matrix-vector accumulation, FP64 full reorthogonalisation
+ * (classical Gram-Schmidt twice per step), FP64 tridiagonal eigenvalues by
+ * bisection on the host.  All K Krylov sequences advance together; a set whose
+ * nev residual bounds beta_m |z_m| meet tol * max(1, |theta|) stops there.
+ *   val_dev: K x nnz float (set-major); 1 <= K <= 256; nev <= 64: eigenvalues
+ *   wanted; max_iter <= 2048: Lanczos steps; tol: relative residual bound on the nev Ritz
+ *   pairs; evals_host: K x nev double (host, ascending; NaN where fewer Ritz
+ *   values exist); evec0_dev: NULL or K x dim double (device), the normalised
+ *   lowest Ritz vector of each set.
+ * Library-allocated for the call: (max_iter + 1) x dim x K double of Lanczos
+ * vectors, the transposed index of the strictly-upper part (nnz - dim int64),
+ * and for K > 1 an element-major copy of the values (K x nnz float).
+ * Deterministic (no atomics in any floating-point sum) as long as no column
+ * holds more than 16384 strictly-upper nonzeros; such a column is summed in
+ * an order that may vary between runs.  Returns 0, or 1 if
+ * some set did not meet tol within max_iter (results still written), or a
+ * CIH_ERR_* code. */
 int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
                        const float *val_dev, int32_t K, int32_t nev, int32_t max_iter,
                        double tol, double *evals_host, double *evec0_dev, void *stream);

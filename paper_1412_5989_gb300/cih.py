@@ -39,6 +39,11 @@ _SIGS = {
     "cih_basis_destroy": [_P],
     "cih_ham_count": [_P, _P, _i64p, _P],
     "cih_ham_fill": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
+    "cih_ham_fill_interleaved": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
+    "cih_tbme_interleave": [C.c_int32, C.c_int64, _P, _P, _P],
+    "cih_set_launch": [_P, C.c_int32, C.c_int32],
+    "cih_autotune_fill": [_P, _P, C.c_int32, C.c_double, _P, C.c_int32, _P, _P, _P, _P,
+                          _i32p, _i32p, C.POINTER(C.c_float)],
     "cih_check": [_P, _P],
     "cih_lanczos_lowest": [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _P, _P],
     "cih_ham_tbme_grad": [_P, _P, C.c_int32, _P, _P, _P],
@@ -105,6 +110,17 @@ def rowptr_scan_static(counts, rowptr=None, stream=None):
         rowptr = torch.empty(n + 1, dtype=torch.int64, device=counts.device)
     _ok(lib.cih_rowptr_scan_static(_ptr(counts), n, _ptr(rowptr), _stream(stream)), "rowptr_scan_static")
     return rowptr
+
+
+def tbme_interleave(tbme, stream=None):
+    """Element-major copy of K tables: out[t * K + k] = tbme[k, t] (device)."""
+    import torch
+    if tbme.dtype != torch.float32 or not tbme.is_cuda or tbme.dim() != 2 or not tbme.is_contiguous():
+        raise ValueError("tbme must be a contiguous float32 CUDA tensor of shape (K, tbme_len)")
+    K, n = tbme.shape
+    out = torch.empty(max(K * n, 1), dtype=torch.float32, device=tbme.device)
+    _ok(lib.cih_tbme_interleave(K, n, _ptr(tbme), _ptr(out), _stream(stream)), "tbme_interleave")
+    return out[: K * n]
 
 
 def tridiag_eigen(diag, offdiag):
@@ -191,19 +207,70 @@ class Basis:
         """Fill pass.  tbme: (K, tbme_len) or (tbme_len,) float32 CUDA tensor.
         Returns (col int32[nnz], val float32[K, nnz])."""
         import torch
-        t = tbme if tbme.dim() == 2 else tbme.unsqueeze(0)
-        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.shape[1] != self.tbme_len:
-            raise ValueError("tbme must be a contiguous float32 CUDA tensor of shape (K, tbme_len)")
+        t = self._check_table(tbme)
         K = t.shape[0]
-        if col is None:
-            col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
-        if val is None:
-            val = torch.empty((K, max(nnz, 1)), dtype=torch.float32, device="cuda")
+        col, val = self._outputs(nnz, K, col, val)
         if e_sp is not None:
             e_sp = e_sp.to(device="cuda", dtype=torch.float64).contiguous()
         _ok(lib.cih_ham_fill(self._h, _ptr(rowptr), K, float(hbar_omega), _ptr(t), _ptr(e_sp),
                              _ptr(col), _ptr(val), _stream(stream)), "ham_fill")
         return col[:nnz], val[:, :nnz]
+
+    def _check_table(self, tbme):
+        import torch
+        t = tbme if tbme.dim() == 2 else tbme.unsqueeze(0)
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.shape[1] != self.tbme_len:
+            raise ValueError("tbme must be a contiguous float32 CUDA tensor of shape (K, tbme_len)")
+        return t
+
+    def _outputs(self, nnz, K, col, val):
+        import torch
+        if col is None:
+            col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        if val is None:
+            val = torch.empty((K, max(nnz, 1)), dtype=torch.float32, device="cuda")
+        return col, val
+
+    def fill_interleaved(self, rowptr, nnz: int, tbme_il, K: int, hbar_omega: float = 20.0, e_sp=None,
+                         stream=None, col=None, val=None):
+        """Fill pass from K element-major tables (tbme_interleave's output,
+        float32 (tbme_len * K,)).  Returns (col int32[nnz], val float32[K, nnz])."""
+        import torch
+        if tbme_il.dtype != torch.float32 or not tbme_il.is_cuda or tbme_il.numel() != K * self.tbme_len:
+            raise ValueError("tbme_il must be a float32 CUDA tensor of K * tbme_len entries")
+        col, val = self._outputs(nnz, K, col, val)
+        if e_sp is not None:
+            e_sp = e_sp.to(device="cuda", dtype=torch.float64).contiguous()
+        _ok(lib.cih_ham_fill_interleaved(self._h, _ptr(rowptr), K, float(hbar_omega), _ptr(tbme_il.contiguous()),
+                                         _ptr(e_sp), _ptr(col), _ptr(val), _stream(stream)), "ham_fill_interleaved")
+        return col[:nnz], val[:, :nnz]
+
+    def set_launch(self, warps_per_cta: int, ctas_per_sm: int = 0):
+        """Launch shape of this basis' row kernels."""
+        _ok(lib.cih_set_launch(self._h, warps_per_cta, ctas_per_sm), "set_launch")
+
+    def autotune_fill(self, rowptr, nnz: int, tbme, hbar_omega: float = 20.0, e_sp=None, *, K: int | None = None,
+                      interleaved: bool = False, stream=None, col=None, val=None):
+        """Time every launch shape of the fill and keep the fastest on this basis.
+        tbme: (K, tbme_len) tables, or with interleaved=True the element-major
+        copy from tbme_interleave (then K must be given).  Returns
+        (col, val, (warps_per_cta, ctas_per_sm, ms))."""
+        import torch
+        if interleaved:
+            if K is None or tbme.numel() != K * self.tbme_len:
+                raise ValueError("interleaved tables need K and K * tbme_len entries")
+            t = tbme.contiguous()
+        else:
+            t = self._check_table(tbme)
+            K = t.shape[0]
+        col, val = self._outputs(nnz, K, col, val)
+        if e_sp is not None:
+            e_sp = e_sp.to(device="cuda", dtype=torch.float64).contiguous()
+        w, c, ms = C.c_int32(), C.c_int32(), C.c_float()
+        _ok(lib.cih_autotune_fill(self._h, _ptr(rowptr), K, float(hbar_omega), _ptr(t), int(interleaved),
+                                  _ptr(e_sp), _ptr(col), _ptr(val), _stream(stream), C.byref(w), C.byref(c),
+                                  C.byref(ms)), "autotune_fill")
+        return col[:nnz], val[:, :nnz], (w.value, c.value, ms.value)
 
     def check(self, stream=None):
         _ok(lib.cih_check(self._h, _stream(stream)), "check")
@@ -213,7 +280,7 @@ class Basis:
         """Lowest nev eigenvalues of each of the K matrices; returns
         (evals (K, nev) float64 numpy, evec0 (K, dim) float64 CUDA or None, converged)."""
         import torch
-        v = val if val.dim() == 2 else val.unsqueeze(0)
+        v = (val if val.dim() == 2 else val.unsqueeze(0)).contiguous()
         K = v.shape[0]
         ev = np.zeros((K, nev))
         vec = torch.empty((K, self.dim), dtype=torch.float64, device="cuda") if want_vectors else None

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -238,7 +239,76 @@ int cih_ham_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hba
     if (rc) return rc;
     if (!rowptr_dev || !col_dev || !val_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
     if (!tbme_dev && h->layout.total > 0) return fail(CIH_ERR_ARG, "NULL two-body table");
-    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, e_sp_dev, col_dev, val_dev, (cudaStream_t)stream);
+    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, false, e_sp_dev, col_dev, val_dev, (cudaStream_t)stream);
+}
+
+int cih_ham_fill_interleaved(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,
+                             const float *tbme_il_dev, const double *e_sp_dev, int32_t *col_dev, float *val_dev,
+                             void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!rowptr_dev || !col_dev || !val_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
+    if (!tbme_il_dev && h->layout.total > 0) return fail(CIH_ERR_ARG, "NULL two-body table");
+    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_il_dev, true, e_sp_dev, col_dev, val_dev,
+                       (cudaStream_t)stream);
+}
+
+int cih_tbme_interleave(int32_t K, int64_t tbme_len, const float *tbme_dev, float *tbme_il_dev, void *stream)
+{
+    if (K < 1 || tbme_len < 0 || (tbme_len > 0 && (!tbme_dev || !tbme_il_dev)))
+        return fail(CIH_ERR_ARG, "bad interleave arguments");
+    return launch_interleave(K, tbme_len, tbme_dev, tbme_il_dev, (cudaStream_t)stream);
+}
+
+int cih_set_launch(cih_basis_h h, int32_t warps_per_cta, int32_t ctas_per_sm)
+{
+    if (!h) return fail(CIH_ERR_ARG, "NULL handle");
+    if ((warps_per_cta != 8 && warps_per_cta != 16) || ctas_per_sm < 0 || ctas_per_sm > 32)
+        return fail(CIH_ERR_ARG, "warps_per_cta must be 8 or 16, ctas_per_sm 0..32");
+    h->launch_warps = warps_per_cta;
+    h->launch_ctas = ctas_per_sm;
+    return CIH_OK;
+}
+
+int cih_autotune_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega, const float *tbme_dev,
+                      int32_t interleaved, const double *e_sp_dev, int32_t *col_dev, float *val_dev, void *stream,
+                      int32_t *best_warps, int32_t *best_ctas, float *best_ms)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!rowptr_dev || !col_dev || !val_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int warps[2] = {16, 8};
+    const int ctas[4] = {0, 1, 2, 3};
+    float best = 1e30f;
+    int bw = 16, bc = 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "autotune events");
+    for (int wi = 0; wi < 2 && !rc; ++wi)
+        for (int ci = 0; ci < 4 && !rc; ++ci) {
+            h->launch_warps = warps[wi];
+            h->launch_ctas = ctas[ci];
+            float ms = 0.0f, tmin = 1e30f;
+            for (int rep = 0; rep < 3 && !rc; ++rep) {
+                cudaEventRecord(e0, st);
+                rc = launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, interleaved != 0, e_sp_dev, col_dev, val_dev, st);
+                cudaEventRecord(e1, st);
+                if (!rc && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+                    rep > 0)
+                    tmin = std::min(tmin, ms);
+            }
+            if (!rc && tmin < best) { best = tmin; bw = warps[wi]; bc = ctas[ci]; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->launch_warps = bw;
+    h->launch_ctas = bc;
+    if (best_warps) *best_warps = bw;
+    if (best_ctas) *best_ctas = bc;
+    if (best_ms) *best_ms = best;
+    return rc;
 }
 
 int cih_check(cih_basis_h h, void *stream)
@@ -268,7 +338,7 @@ int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *
     int rc = needs_device(h);
     if (rc) return rc;
     if (!rowptr_dev || !col_dev || !val_dev || !evals_host) return fail(CIH_ERR_ARG, "NULL array");
-    if (K < 1 || nev < 1 || nev > 64 || max_iter < 1 || max_iter > 2048 || !(tol > 0))
+    if (K < 1 || K > 256 || nev < 1 || nev > 64 || max_iter < 1 || max_iter > 2048 || !(tol > 0))
         return fail(CIH_ERR_ARG, "K, nev, max_iter or tol out of range");
     return guarded([&]() -> int {
         return lanczos(*h, rowptr_dev, col_dev, val_dev, K, nev, max_iter, tol, evals_host, evec0_dev,

@@ -166,6 +166,8 @@ struct cih_basis {
     int device = 0;
     cudaMemPool_t pool = nullptr;             // library pool the handle's buffers come from
     cudaStream_t stream = nullptr;            // stream of the build
+    int launch_warps = 16;                    // row kernels: warps per CTA (8 or 16)
+    int launch_ctas = 0;                      // row kernels: CTAs per SM (0 = as many as fit)
 };
 
 namespace cih {
@@ -199,8 +201,9 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st);
 // kernels (ham.cu)
 int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
 int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
-int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme,
+int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved,
                 const double *esp, int32_t *col, float *val, cudaStream_t st);
+int launch_interleave(int K, int64_t len, const float *in, float *out, cudaStream_t st);
 int launch_grad(const cih_basis &b, const int64_t *rowptr, int K, const double *psi,
                 unsigned long long *acc, cudaStream_t st);
 int launch_grad_finish(int64_t n, const unsigned long long *acc, double *grad, cudaStream_t st);
@@ -212,6 +215,9 @@ int64_t scan_scratch_needed(int64_t n);
 
 // symmetric tridiagonal eigenproblem, ascending, Z row-major n x n (tridiag.cpp)
 void tridiag_qr(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &Z);
+// r-th smallest eigenvalue by bisection, and its normalised eigenvector by inverse iteration
+double tridiag_eigenvalue(int n, const double *d, const double *e, int r);
+void tridiag_eigenvector(int n, const double *d, const double *e, double theta, double *z);
 
 // Lanczos (lanczos.cu)
 int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val,

@@ -23,55 +23,34 @@
 // spectators k in R in ascending combined order.  Proton and neutron moves
 // of a pn element factorise (the cross-species counts cancel in pairs).
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "cih_internal.h"
 
 namespace cih {
 namespace {
 
-constexpr int kWarpsPerBlock = 8;
+// What the fill writes and reads: K two-body sets, table entry t of set k at
+// tbme[k * tb_sk + t * tb_si] (set-major: tb_sk = table length, tb_si = 1;
+// interleaved: tb_sk = 1, tb_si = K).
+struct FillArgs {
+    int K;
+    double hw;
+    const float *tbme;
+    int64_t tb_sk, tb_si;
+    const double *esp;        // combined orbital energies or null
+    int32_t *col;
+    float *val;               // K x nnz
+};
 
-template <int W>
-__device__ __forceinline__ void ld_bits(const uint64_t *base, int64_t i, uint64_t (&o)[W])
-{
-#pragma unroll
-    for (int w = 0; w < W; ++w) o[w] = base[i * W + w];
-}
+struct GradArgs {
+    int K;
+    const double *psi;        // K x dim
+    unsigned long long *acc;  // K x tbme_len fixed point
+};
 
-template <int W>
-__device__ __forceinline__ int popc_xor(const uint64_t (&a)[W], const uint64_t (&b)[W])
-{
-    int c = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) c += __popcll(a[w] ^ b[w]);
-    return c;
-}
-
-// number of set bits of R strictly below bit k
-template <int W>
-__device__ __forceinline__ int below(const uint64_t (&R)[W], int k)
-{
-    int c = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        int lo = w * 64;
-        if (k >= lo + 64) c += __popcll(R[w]);
-        else if (k > lo) c += __popcll(R[w] & ((1ull << (k - lo)) - 1));
-    }
-    return c;
-}
-
-template <int W>
-__device__ __forceinline__ int lowest_bit(const uint64_t (&x)[W])
-{
-#pragma unroll
-    for (int w = 0; w < W; ++w)
-        if (x[w]) return w * 64 + __ffsll((long long)x[w]) - 1;
-    return -1;
-}
-
-template <int W>
-__device__ __forceinline__ void clear_bit(uint64_t (&x)[W], int k) { x[k >> 6] &= ~(1ull << (k & 63)); }
+constexpr double kFixScale = 72057594037927936.0;   // 2^56
 
 // Table index of V(ab, cd) for combined orbitals in any order; false if the
 // pairs are not one table entry (a bug in the walk: flagged by the caller).
@@ -90,231 +69,6 @@ __device__ __forceinline__ bool tbme_at(const DevBasis &B, int a, int b, int c, 
     int64_t n = B.gsize[g];
     idx = B.goff[g] + u * n - u * (u - 1) / 2 + (v - u);
     return true;
-}
-
-enum Kind : int { kDiag = 0, kP1 = 1, kN1 = 2, kP2 = 3, kN2 = 4, kPN = 5 };
-
-// Everything that identifies one matrix element's terms.
-template <int W>
-struct Elem {
-    int kind;
-    int sign;                 // sign of the whole two-body part
-    int a, b, c, d;           // combined orbitals: a(,b) bra-only, c(,d) ket-only
-    uint64_t rp[W], rn[W];    // spectators: common protons / neutrons
-};
-
-// Visit the two-body terms (table index, sign) of an element in the fixed
-// order the values are summed in.
-template <int W, class F>
-__device__ __forceinline__ bool for_terms(const DevBasis &B, const Elem<W> &e, F &&f)
-{
-    int64_t idx;
-    int s;
-    const int nbase = B.sp[1].orb_base;
-    switch (e.kind) {
-    case kP2:
-    case kN2:
-    case kPN:
-        if (!tbme_at(B, e.a, e.b, e.c, e.d, idx, s)) return false;
-        f(idx, s * e.sign);
-        return true;
-    case kP1:
-    case kN1: {
-        // spectators ascending in combined order: protons, then neutrons
-        for (int sp = 0; sp < 2; ++sp) {
-            const uint64_t *R = sp == 0 ? e.rp : e.rn;
-            int off = sp == 0 ? 0 : nbase;
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                uint64_t m = R[w];
-                while (m) {
-                    int k = off + w * 64 + __ffsll((long long)m) - 1;
-                    m &= m - 1;
-                    if (!tbme_at(B, e.a, k, e.c, k, idx, s)) return false;
-                    f(idx, s * e.sign);
-                }
-            }
-        }
-        return true;
-    }
-    default: {  // diagonal: all occupied pairs a<b, lexicographic
-        for (int sa = 0; sa < 2; ++sa) {
-            const uint64_t *Ra = sa == 0 ? e.rp : e.rn;
-            int offa = sa == 0 ? 0 : nbase;
-            for (int wa = 0; wa < W; ++wa) {
-                uint64_t ma = Ra[wa];
-                while (ma) {
-                    int ka = wa * 64 + __ffsll((long long)ma) - 1;
-                    ma &= ma - 1;
-                    int A = offa + ka;
-                    for (int sb = sa; sb < 2; ++sb) {
-                        const uint64_t *Rb = sb == 0 ? e.rp : e.rn;
-                        int offb = sb == 0 ? 0 : nbase;
-                        for (int wb = 0; wb < W; ++wb) {
-                            uint64_t mb = Rb[wb];
-                            while (mb) {
-                                int kb = wb * 64 + __ffsll((long long)mb) - 1;
-                                mb &= mb - 1;
-                                int Bc = offb + kb;
-                                if (Bc <= A) continue;
-                                if (!tbme_at(B, A, Bc, A, Bc, idx, s)) return false;
-                                f(idx, s);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        return true;
-    }
-    }
-}
-
-// ---------------------------------------------------------------- element set-up
-
-template <int W>
-__device__ __forceinline__ void make_diag(Elem<W> &e, const uint64_t (&pb)[W], const uint64_t (&nb)[W])
-{
-    e.kind = kDiag;
-    e.sign = 1;
-#pragma unroll
-    for (int w = 0; w < W; ++w) { e.rp[w] = pb[w]; e.rn[w] = nb[w]; }
-}
-
-// one orbital moved within species `sp` (bra bits x, ket bits y), other species `o` unchanged
-template <int W>
-__device__ __forceinline__ void make_one(Elem<W> &e, int sp, int base, const uint64_t (&x)[W], const uint64_t (&y)[W],
-                                         const uint64_t (&o)[W])
-{
-    uint64_t R[W], dx[W], dy[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) { R[w] = x[w] & y[w]; dx[w] = x[w] & ~y[w]; dy[w] = y[w] & ~x[w]; }
-    int a = lowest_bit<W>(dx), c = lowest_bit<W>(dy);
-    e.kind = sp == 0 ? kP1 : kN1;
-    e.sign = ((below<W>(R, a) + below<W>(R, c)) & 1) ? -1 : 1;
-    e.a = base + a;
-    e.c = base + c;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        e.rp[w] = sp == 0 ? R[w] : o[w];
-        e.rn[w] = sp == 0 ? o[w] : R[w];
-    }
-}
-
-// two orbitals moved within one species
-template <int W>
-__device__ __forceinline__ void make_two(Elem<W> &e, int sp, int base, const uint64_t (&x)[W], const uint64_t (&y)[W])
-{
-    uint64_t R[W], dx[W], dy[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) { R[w] = x[w] & y[w]; dx[w] = x[w] & ~y[w]; dy[w] = y[w] & ~x[w]; }
-    int a = lowest_bit<W>(dx); clear_bit<W>(dx, a);
-    int b = lowest_bit<W>(dx);
-    int c = lowest_bit<W>(dy); clear_bit<W>(dy, c);
-    int d = lowest_bit<W>(dy);
-    e.kind = sp == 0 ? kP2 : kN2;
-    e.sign = ((below<W>(R, a) + below<W>(R, b) + below<W>(R, c) + below<W>(R, d)) & 1) ? -1 : 1;
-    e.a = base + a; e.b = base + b; e.c = base + c; e.d = base + d;
-}
-
-// one proton and one neutron moved
-template <int W>
-__device__ __forceinline__ void make_pn(Elem<W> &e, int nbase, const uint64_t (&px)[W], const uint64_t (&py)[W],
-                                        const uint64_t (&nx)[W], const uint64_t (&ny)[W])
-{
-    uint64_t Rp[W], Rn[W], dpx[W], dpy[W], dnx[W], dny[W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        Rp[w] = px[w] & py[w]; dpx[w] = px[w] & ~py[w]; dpy[w] = py[w] & ~px[w];
-        Rn[w] = nx[w] & ny[w]; dnx[w] = nx[w] & ~ny[w]; dny[w] = ny[w] & ~nx[w];
-    }
-    int a = lowest_bit<W>(dpx), c = lowest_bit<W>(dpy);
-    int b = lowest_bit<W>(dnx), d = lowest_bit<W>(dny);
-    e.kind = kPN;
-    e.sign = ((below<W>(Rp, a) + below<W>(Rp, c) + below<W>(Rn, b) + below<W>(Rn, d)) & 1) ? -1 : 1;
-    e.a = a; e.b = nbase + b; e.c = c; e.d = nbase + d;
-}
-
-// ---------------------------------------------------------------- the row walk
-
-struct FillArgs {
-    int K;
-    double hw;
-    const float *tbme;        // K x tbme_len
-    const double *esp;        // combined orbital energies or null
-    int32_t *col;
-    float *val;               // K x nnz
-    int64_t nnz;
-};
-
-struct GradArgs {
-    int K;
-    const double *psi;        // K x dim
-    unsigned long long *acc;  // K x tbme_len fixed point
-};
-
-constexpr double kFixScale = 72057594037927936.0;   // 2^56
-
-template <int W>
-__device__ double one_body(const DevBasis &B, const FillArgs &F, const uint64_t (&pb)[W], const uint64_t (&nb)[W])
-{
-    double s = 0.0;
-    for (int sp = 0; sp < 2; ++sp) {
-        const uint64_t *R = sp == 0 ? pb : nb;
-        int off = B.sp[sp].orb_base;
-        for (int w = 0; w < W; ++w) {
-            uint64_t m = R[w];
-            while (m) {
-                int k = off + w * 64 + __ffsll((long long)m) - 1;
-                m &= m - 1;
-                s += F.esp ? F.esp[k] : F.hw * ((double)B.orbN[k] + 1.5);
-            }
-        }
-    }
-    return s;
-}
-
-// Mode 0: count, 1: fill, 2: gradient
-template <int W, int MODE>
-__device__ __forceinline__ void emit(const DevBasis &B, const FillArgs &F, const GradArgs &G, int *status,
-                                     int64_t pos, int64_t lim, int64_t row, int64_t colj, const Elem<W> &e,
-                                     double diag1)
-{
-    if (MODE == 1) {
-        if (pos >= lim) {                      // never for a consistent count: refuse the write
-            atomicOr(status, 2);
-            return;
-        }
-        F.col[pos] = (int32_t)colj;
-        for (int k = 0; k < F.K; ++k) {
-            const float *T = F.tbme + (int64_t)k * B.tbme_len;
-            double s = e.kind == kDiag ? diag1 : 0.0;
-            bool ok = for_terms<W>(B, e, [&](int64_t idx, int sg) { s += sg * (double)T[idx]; });
-            if (!ok) atomicOr(status, 1);
-            F.val[(int64_t)k * F.nnz + pos] = (float)s;
-        }
-    } else if (MODE == 2) {
-        for (int k = 0; k < G.K; ++k) {
-            const double *psi = G.psi + (int64_t)k * B.dim;
-            double f = (colj == row ? 1.0 : 2.0) * psi[row] * psi[colj];
-            unsigned long long *acc = G.acc + (int64_t)k * B.tbme_len;
-            bool ok = for_terms<W>(B, e, [&](int64_t idx, int sg) {
-                long long q = __double2ll_rn(sg * f * kFixScale);
-                atomicAdd(acc + idx, (unsigned long long)q);
-            });
-            if (!ok) atomicOr(status, 1);
-        }
-    }
-}
-
-// first index in sorted list[lo, hi) whose value is >= key
-__device__ __forceinline__ int64_t lower_bound(const int32_t *list, int64_t lo, int64_t hi, int32_t key)
-{
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (list[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
 }
 
 // ---------------------------------------------------------------- row kernel
@@ -336,8 +90,6 @@ __device__ __forceinline__ int64_t lower_bound(const int32_t *list, int64_t lo, 
 //   deferred  - one-move elements, lanes over (element, spectator) pairs and
 //               a segmented FP64 reduction.
 
-constexpr int kWarps = 16;
-constexpr int kThreads = kWarps * 32;
 constexpr int kGroupCap = 128;
 constexpr int kSlowCap = 64;
 constexpr int kMaxA = 64;
@@ -359,10 +111,13 @@ constexpr int w_scol = w_spos + kSlowCap * 4;              // int32[kSlowCap]
 constexpr int w_scode = w_scol + kSlowCap * 4;             // uint32[kSlowCap]
 constexpr int w_occ = w_scode + kSlowCap * 4;              // int16[kMaxA]
 constexpr int w_size = (w_occ + kMaxA * 2 + 15) / 16 * 16;
-constexpr int S = warp0 + kWarps * w_size;                 // int16[n_orb_p * G]
+// the pn split table S (int16[n_orb_p * G]) follows the per-warp areas
+template <int WARPS>
+constexpr int S = warp0 + WARPS * w_size;
 }  // namespace sm
 
-__host__ __device__ inline size_t smem_bytes(int nS) { return (size_t)sm::S + ((size_t)nS * 2 + 15) / 16 * 16; }
+template <int WARPS>
+inline size_t smem_bytes(int nS) { return (size_t)sm::S<WARPS> + ((size_t)nS * 2 + 15) / 16 * 16; }
 
 template <class T>
 __device__ __forceinline__ T *sptr(unsigned char *base, int off) { return reinterpret_cast<T *>(base + off); }
@@ -374,9 +129,10 @@ __device__ __forceinline__ double warp_sum(double v, int width)
 }
 
 // table index of a pn element from the candidate (uv, mv) and neutron move (ni)
+template <int WARPS>
 __device__ __forceinline__ int pn_index(const unsigned char *sb, uint32_t uv, uint32_t mv, uint32_t ni, int &sign)
 {
-    const int16_t *S = reinterpret_cast<const int16_t *>(sb + sm::S);
+    const int16_t *S = reinterpret_cast<const int16_t *>(sb + sm::S<WARPS>);
     const int32_t *gs = reinterpret_cast<const int32_t *>(sb + sm::gsize);
     const int32_t *go = reinterpret_cast<const int32_t *>(sb + sm::goff);
     const int t = (int)((ni >> 16) & 0x7F) - 64 + (int)(((mv >> 8) ^ (ni >> 23)) & 1);
@@ -404,11 +160,11 @@ __device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F,
     if (MODE == 1) {
         R.col[e] = (int32_t)colj;
         if (K1) {
-            const float v = __ldg(F.tbme + idx);
+            const float v = __ldg(F.tbme + (int64_t)idx * F.tb_si);
             R.val[e] = sgn ? -v : v;
         } else {
             for (int k = 0; k < F.K; ++k) {
-                const float v = __ldg(F.tbme + (int64_t)k * B.tbme_len + idx);
+                const float v = __ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)idx * F.tb_si);
                 R.val[(int64_t)k * R.nnz + e] = sgn ? -v : v;
             }
         }
@@ -464,7 +220,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const FillArgs &F,
         for (int kk = 0; kk < (MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++kk) {
             if (MODE == 1) {
                 double v = 0.0;
-                if (has && ok) v = sg * (double)__ldg(F.tbme + (int64_t)kk * B.tbme_len + idx);
+                if (has && ok) v = sg * (double)__ldg(F.tbme + (int64_t)kk * F.tb_sk + idx * F.tb_si);
                 v = warp_sum(v, gsz);
                 if (act && i == 0) {
                     if (kk == 0) R.col[eo] = (int32_t)colj;
@@ -481,10 +237,11 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const FillArgs &F,
     nslow = 0;
 }
 
-template <int W, int MODE, bool K1>
-__global__ void __launch_bounds__(kThreads, 2)
+template <int W, int MODE, bool K1, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
 k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs Gr, int *status)
 {
+    constexpr int kThreads = WARPS * 32;
     extern __shared__ __align__(16) unsigned char sb[];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned lt = (1u << lane) - 1;
@@ -493,7 +250,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     const int npairs = A * (A - 1) / 2;
     if (MODE != 0) {
         const int G = B.pn_G, nS = SP.n_orb * G;
-        int16_t *S = sptr<int16_t>(sb, sm::S);
+        int16_t *S = sptr<int16_t>(sb, sm::S<WARPS>);
         int32_t *gs = sptr<int32_t>(sb, sm::gsize), *go = sptr<int32_t>(sb, sm::goff);
         for (int i = tid; i < nS; i += kThreads) S[i] = B.pn_S[i];
         for (int i = tid; i < G; i += kThreads) { gs[i] = B.pn_gsize[i]; go[i] = B.pn_goff[i]; }
@@ -555,7 +312,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                         continue;
                     }
                     if (MODE == 1) {
-                        acc += sg * (double)__ldg(F.tbme + (int64_t)k * B.tbme_len + idx);
+                        acc += sg * (double)__ldg(F.tbme + (int64_t)k * F.tb_sk + idx * F.tb_si);
                     } else {
                         const double pr = Gr.psi[(int64_t)k * B.dim + row];
                         const long long qv = __double2ll_rn(sg * pr * pr * kFixScale);
@@ -699,7 +456,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                             const int at = sg4.w + tt + (tt >= w_ins[j] ? 1 : 0);
                             const int2 ent = n1row[w_n1s[j] + tt];
                             int sg;
-                            const int idx = pn_index(sb, (uint32_t)sg4.y, (uint32_t)sg4.z, (uint32_t)ent.y, sg);
+                            const int idx = pn_index<WARPS>(sb, (uint32_t)sg4.y, (uint32_t)sg4.z, (uint32_t)ent.y, sg);
                             put_single<MODE, K1>(B, F, Gr, R, at, (int64_t)(sg4.x + ent.x), idx, sg);
                         }
                     }
@@ -714,6 +471,49 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     }
 }
 
+// Raise a kernel's dynamic shared-memory limit on a device once per size, so
+// that later calls (inside a stream capture, say) only launch.
+cudaError_t raise_smem_limit(const void *kern, int dev, int bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> raised;
+    std::lock_guard<std::mutex> lock(mu);
+    int &have = raised[{kern, dev}];
+    if (bytes <= have) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
+
+template <int MODE, int WARPS>
+int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, const FillArgs &F, const GradArgs &G,
+                  cudaStream_t st)
+{
+    const DevBasis &D = b.dev;
+    const size_t smem = MODE == 0 ? (size_t)sm::S<WARPS> : smem_bytes<WARPS>(D.sp[0].n_orb * D.pn_G);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto go = [&](auto kern) -> int {
+        cudaError_t ee = raise_smem_limit((const void *)kern, dev, (int)smem);
+        if (ee != cudaSuccess) return cuda_fail(ee, "row kernel shared memory");
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+        per_sm = std::max(per_sm, 1);
+        if (b.launch_ctas > 0) per_sm = std::min(per_sm, b.launch_ctas);
+        const int64_t want = (b.dim + WARPS - 1) / WARPS;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, want));
+        count_launches(1);
+        kern<<<grid, WARPS * 32, smem, st>>>(D, rowptr, counts, F, G, b.dev_status);
+        ee = cudaGetLastError();
+        return ee == cudaSuccess ? CIH_OK : cuda_fail(ee, "row kernel launch");
+    };
+    const bool k1 = MODE == 1 && F.K == 1;
+    if (b.W == 1) return k1 ? go(k_rows<1, MODE, true, WARPS>) : go(k_rows<1, MODE, false, WARPS>);
+    if (b.W == 2) return k1 ? go(k_rows<2, MODE, true, WARPS>) : go(k_rows<2, MODE, false, WARPS>);
+    return k1 ? go(k_rows<4, MODE, true, WARPS>) : go(k_rows<4, MODE, false, WARPS>);
+}
+
 template <int MODE>
 int launch_rows(const cih_basis &b, const int64_t *rowptr, int64_t *counts, const FillArgs &F, const GradArgs &G,
                 cudaStream_t st)
@@ -723,26 +523,18 @@ int launch_rows(const cih_basis &b, const int64_t *rowptr, int64_t *counts, cons
     if (D.pn_G > kGroupCap || D.A > kMaxA || D.A - 1 > 32)
         return fail(CIH_ERR_UNSUPPORTED, "more than 33 particles or pn groups above the row kernel's capacity");
     if (D.tbme_len > INT32_MAX) return fail(CIH_ERR_UNSUPPORTED, "two-body table above 2^31 entries");
-    const size_t smem = MODE == 0 ? (size_t)sm::S : smem_bytes(D.sp[0].n_orb * D.pn_G);
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    auto go = [&](auto kern) -> int {
-        cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (ee != cudaSuccess) return cuda_fail(ee, "row kernel shared memory");
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-        const int64_t want = (b.dim + kWarps - 1) / kWarps;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), want));
-        count_launches(1);
-        kern<<<grid, kThreads, smem, st>>>(D, rowptr, counts, F, G, b.dev_status);
-        ee = cudaGetLastError();
-        return ee == cudaSuccess ? CIH_OK : cuda_fail(ee, "row kernel launch");
-    };
-    const bool k1 = MODE == 1 && F.K == 1;
-    if (b.W == 1) return k1 ? go(k_rows<1, MODE, true>) : go(k_rows<1, MODE, false>);
-    if (b.W == 2) return k1 ? go(k_rows<2, MODE, true>) : go(k_rows<2, MODE, false>);
-    return k1 ? go(k_rows<4, MODE, true>) : go(k_rows<4, MODE, false>);
+    return b.launch_warps == 8 ? launch_rows_w<MODE, 8>(b, rowptr, counts, F, G, st)
+                               : launch_rows_w<MODE, 16>(b, rowptr, counts, F, G, st);
+}
+
+// element-major copy of K set-major tables: out[t * K + k] = in[k * len + t]
+__global__ void k_interleave(int K, int64_t len, const float *in, float *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len * K; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / K;
+        const int k = (int)(i - t * K);
+        out[i] = in[(int64_t)k * len + t];
+    }
 }
 
 __global__ void k_fix_to_double(int64_t n, const unsigned long long *acc, double *out)
@@ -763,11 +555,21 @@ int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st)
     return exclusive_scan_i64(rowptr, b.dim, b.scan_scratch, b.scan_scratch_len, st);
 }
 
-int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme,
+int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved,
                 const double *esp, int32_t *col, float *val, cudaStream_t st)
 {
-    FillArgs F{K, hw, tbme, esp, col, val, 0};
+    FillArgs F{K, hw, tbme, interleaved ? 1 : b.layout.total, interleaved ? (int64_t)K : 1, esp, col, val};
     return launch_rows<1>(b, rowptr, nullptr, F, GradArgs{}, st);
+}
+
+int launch_interleave(int K, int64_t len, const float *in, float *out, cudaStream_t st)
+{
+    if (len * K == 0) return CIH_OK;
+    const int blocks = (int)std::min<int64_t>((len * K + 255) / 256, 152 * 16);
+    count_launches(1);
+    k_interleave<<<blocks, 256, 0, st>>>(K, len, in, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CIH_OK : cuda_fail(e, "interleave");
 }
 
 int launch_grad(const cih_basis &b, const int64_t *rowptr, int K, const double *psi,

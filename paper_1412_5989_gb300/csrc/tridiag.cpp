@@ -63,6 +63,82 @@ void tridiag_qr(int n, std::vector<double> &d, std::vector<double> e, std::vecto
     Z.swap(Z2);
 }
 
+// Number of eigenvalues of the tridiagonal (d, e) below x: negative pivots of
+// the LDL^T factorisation of T - x I (Sylvester's law of inertia).
+static int count_below(int n, const double *d, const double *e, double x)
+{
+    int neg = 0;
+    double q = 1.0;
+    for (int k = 0; k < n; ++k) {
+        q = d[k] - x - (k ? e[k - 1] * e[k - 1] / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        neg += q < 0.0;
+    }
+    return neg;
+}
+
+// r-th smallest eigenvalue by bisection between Gershgorin bounds
+double tridiag_eigenvalue(int n, const double *d, const double *e, int r)
+{
+    double lo = d[0], hi = d[0];
+    for (int k = 0; k < n; ++k) {
+        const double rad = (k ? std::fabs(e[k - 1]) : 0.0) + (k + 1 < n ? std::fabs(e[k]) : 0.0);
+        lo = std::min(lo, d[k] - rad);
+        hi = std::max(hi, d[k] + rad);
+    }
+    for (int it = 0; it < 300; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (count_below(n, d, e, mid) > r) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// normalised eigenvector for the eigenvalue estimate theta: three steps of
+// inverse iteration, (T - theta I) z_new = z, solved by Gaussian elimination
+// with partial pivoting on the tridiagonal
+void tridiag_eigenvector(int n, const double *d, const double *e, double theta, double *z)
+{
+    std::vector<double> a(n), b(n), c(n);     // sub, main, super
+    const double scale = 1e-14 * (std::fabs(theta) + 1.0);
+    for (int k = 0; k < n; ++k) z[k] = 1.0 / std::sqrt((double)n) * (1.0 + 0.1 * ((k * 7919) % 13));
+    for (int step = 0; step < 3; ++step) {
+        for (int k = 0; k < n; ++k) {
+            a[k] = k ? e[k - 1] : 0.0;
+            b[k] = d[k] - theta;
+            c[k] = k + 1 < n ? e[k] : 0.0;
+            if (b[k] == 0.0) b[k] = scale;
+        }
+        // elimination with pivoting: rows k and k+1, keeping two superdiagonals
+        std::vector<double> r2(n, 0.0), rhs(z, z + n);
+        for (int k = 0; k + 1 < n; ++k) {
+            if (std::fabs(a[k + 1]) > std::fabs(b[k])) {       // swap rows k and k+1
+                std::swap(b[k], a[k + 1]);
+                std::swap(c[k], b[k + 1]);
+                std::swap(r2[k], c[k + 1]);
+                std::swap(rhs[k], rhs[k + 1]);
+            }
+            if (b[k] == 0.0) b[k] = scale;
+            const double f = a[k + 1] / b[k];
+            b[k + 1] -= f * c[k];
+            c[k + 1] -= f * r2[k];
+            rhs[k + 1] -= f * rhs[k];
+            a[k + 1] = 0.0;
+        }
+        if (b[n - 1] == 0.0) b[n - 1] = scale;
+        for (int k = n - 1; k >= 0; --k) {
+            double x = rhs[k];
+            if (k + 1 < n) x -= c[k] * z[k + 1];
+            if (k + 2 < n) x -= r2[k] * z[k + 2];
+            z[k] = x / b[k];
+        }
+        double nrm = 0.0;
+        for (int k = 0; k < n; ++k) nrm += z[k] * z[k];
+        nrm = std::sqrt(nrm);
+        for (int k = 0; k < n; ++k) z[k] /= nrm;
+    }
+}
+
 }  // namespace cih
 
 extern "C" int cih_tridiag_eigen(int32_t n, const double *diag, const double *offdiag, double *evals,
