@@ -203,6 +203,47 @@ int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *
 int cih_ham_tbme_grad(cih_basis_h h, const int64_t *rowptr_dev, int32_t K,
                       const double *psi_dev, double *grad_dev, void *stream);
 
+/* One instance of a batch for cih_batch_solve: a basis with its own K
+ * two-body tables.  Instances of one batch may differ in size, particle
+ * numbers and Nmax. */
+typedef struct {
+    cih_basis_h basis;        /* in: from cih_basis_enumerate */
+    int32_t K;                /* in: interaction sets of this instance, >= 1 */
+    const float *tbme_dev;    /* in: K x tbme_len float, set-major (device) */
+    const double *e_sp_dev;   /* in: NULL (HO energies) or n_orb_p + n_orb_n double (device) */
+    double *evals_host;       /* out: K x nev double (host), ascending */
+    double *grad_dev;         /* out: NULL, or K x tbme_len double (device): d E0 / d t */
+    int64_t nnz;              /* out: stored nonzeros, from the count pass */
+    int64_t bytes;            /* out: device bytes the instance holds while it is solved */
+    int32_t wave;             /* out: admission wave it ran in, -1 if not admitted */
+    int32_t status;           /* out: 0 converged, 1 not converged within max_iter,
+                                 CIH_ERR_CAPACITY alone above the budget, or another CIH_ERR_* */
+} cih_instance_t;
+
+/* Fused build + Lanczos + adjoint for a batch of instances (Sec. 4.1's
+ * count-then-compute passes, Sec. 2's Lanczos, and the Hellmann-Feynman
+ * adjoint of cih_ham_tbme_grad), with admission by device memory:
+ *   1. every instance's count pass and row-pointer scan (one concurrent
+ *      branch per instance), then its nonzero count nnz;
+ *   2. from nnz, each instance's bytes: rowptr, col, K x nnz values and the
+ *      lowest Ritz vectors (held for the wave), plus the Lanczos and adjoint
+ *      scratch (held one instance at a time);
+ *   3. instances are admitted in the given order into waves whose peak stays
+ *      within hbm_budget bytes (0 = 90% of the free device memory at the
+ *      call); an instance above the budget on its own gets CIH_ERR_CAPACITY
+ *      and is skipped;
+ *   4. per wave: the fills of all its instances as one CUDA graph launch
+ *      (one branch per instance), then per instance the lowest nev
+ *      eigenvalues by Lanczos (as cih_lanczos_lowest with max_iter, tol) and,
+ *      when grad_dev is given, d E0 / d t by the adjoint of the lowest Ritz
+ *      vector; the wave's memory is released before the next wave.
+ * All device memory is library-allocated for the call, except the caller's
+ * tables and gradients.  Synchronises `stream`.  Returns 0 if every instance
+ * has status 0, 1 if some instance has another status (see inst[i].status),
+ * or a CIH_ERR_* code for the call itself (bad arguments, CUDA failure). */
+int cih_batch_solve(cih_instance_t *inst, int32_t n, double hbar_omega, int32_t nev, int32_t max_iter,
+                    double tol, int64_t hbm_budget, void *stream);
+
 /* Synchronise `stream`, read and clear the basis' device error word.
  * Returns CIH_ERR_DEVICE if a kernel met a pair outside the table layout
  * (which the walk never produces for a consistent basis), else 0. */

@@ -30,6 +30,12 @@ class Space(C.Structure):
     _fields_ = [("Z", C.c_int32), ("N", C.c_int32), ("Nmax", C.c_int32), ("twoM", C.c_int32)]
 
 
+class Instance(C.Structure):
+    _fields_ = [("basis", _P), ("K", C.c_int32), ("tbme_dev", _P), ("e_sp_dev", _P), ("evals_host", _dp),
+                ("grad_dev", _P), ("nnz", C.c_int64), ("bytes", C.c_int64), ("wave", C.c_int32),
+                ("status", C.c_int32)]
+
+
 _SIGS = {
     "cih_basis_enumerate": [C.POINTER(Space), C.POINTER(_P), _P],
     "cih_basis_host_only": [C.POINTER(Space), C.POINTER(_P)],
@@ -45,6 +51,7 @@ _SIGS = {
     "cih_autotune_fill": [_P, _P, C.c_int32, C.c_double, _P, C.c_int32, _P, _P, _P, _P,
                           _i32p, _i32p, C.POINTER(C.c_float)],
     "cih_check": [_P, _P],
+    "cih_batch_solve": [C.POINTER(Instance), C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int64, _P],
     "cih_lanczos_lowest": [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _P, _P],
     "cih_ham_tbme_grad": [_P, _P, C.c_int32, _P, _P, _P],
     "cih_tridiag_eigen": [C.c_int32, _dp, _dp, _dp, _dp],
@@ -297,6 +304,87 @@ class Basis:
         g = torch.empty((K, max(self.tbme_len, 1)), dtype=torch.float64, device="cuda")
         _ok(lib.cih_ham_tbme_grad(self._h, _ptr(rowptr), K, _ptr(p), _ptr(g), _stream(stream)), "ham_tbme_grad")
         return g[:, : self.tbme_len]
+
+
+def solve_batch(items, hbar_omega: float = 20.0, nev: int = 5, max_iter: int = 300, tol: float = 1e-8,
+                hbm_budget: int = 0, want_grad: bool = True, stream=None):
+    """Fused count -> admission -> fill -> Lanczos -> adjoint over instances of
+    different sizes (cih_batch_solve).  items: list of (Basis, tbme (K, tbme_len)
+    float32 CUDA tensor[, e_sp]).  Returns (rc, list of dicts with evals (K, nev),
+    grad (K, tbme_len) float64 CUDA tensor or None, nnz, bytes, wave, status)."""
+    import torch
+    n = len(items)
+    arr = (Instance * max(n, 1))()
+    keep = []
+    for i, it in enumerate(items):
+        B, t = it[0], it[1]
+        e_sp = it[2] if len(it) > 2 else None
+        t = B._check_table(t)
+        K = t.shape[0]
+        ev = np.full((K, nev), np.nan)
+        g = torch.empty((K, max(B.tbme_len, 1)), dtype=torch.float64, device="cuda") if want_grad else None
+        if e_sp is not None:
+            e_sp = e_sp.to(device="cuda", dtype=torch.float64).contiguous()
+        keep.append((B, t, ev, g, e_sp))
+        arr[i] = Instance(B._h, K, _ptr(t), _ptr(e_sp), ev.ctypes.data_as(_dp), _ptr(g), 0, 0, -1, 0)
+    rc = _ok(lib.cih_batch_solve(arr, n, float(hbar_omega), nev, max_iter, float(tol), int(hbm_budget),
+                                 _stream(stream)), "batch_solve")
+    out = []
+    for i, (B, t, ev, g, _) in enumerate(keep):
+        x = arr[i]
+        out.append(dict(evals=ev, grad=None if g is None else g[:, : B.tbme_len], nnz=x.nnz, bytes=x.bytes,
+                        wave=x.wave, status=x.status))
+    return rc, out
+
+
+def lowest_eigenvalue(basis: Basis, tbme, hbar_omega: float = 20.0, e_sp=None, max_iter: int = 400,
+                      tol: float = 1e-10):
+    """E0 of each of the K matrices, differentiable w.r.t. the two-body tables:
+    the backward pass is the library's adjoint (cih_ham_tbme_grad) applied to
+    the lowest Ritz vectors.  tbme: (K, tbme_len) or (tbme_len,) float32 CUDA."""
+    return _LowestEigenvalue.apply(tbme, basis, float(hbar_omega), e_sp, int(max_iter), float(tol))
+
+
+def _lowest_eigenvalue_function():
+    import torch
+
+    class LowestEigenvalue(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, tbme, basis, hbar_omega, e_sp, max_iter, tol):
+            t = tbme.detach()
+            squeeze = t.dim() == 1
+            t = (t.unsqueeze(0) if squeeze else t).contiguous()
+            rowptr, col, val, nnz = build_hamiltonian(basis, t, hbar_omega, e_sp)
+            ev, psi, conv = basis.lanczos(rowptr, col, val, nev=1, max_iter=max_iter, tol=tol)
+            if not conv:
+                raise CihError(1, "lowest_eigenvalue: Lanczos did not converge")
+            del col, val
+            ctx.basis, ctx.squeeze = basis, squeeze
+            ctx.save_for_backward(rowptr, psi)
+            e0 = torch.from_numpy(ev[:, 0].copy()).to(tbme.device)
+            return e0[0] if squeeze else e0
+
+        @staticmethod
+        def backward(ctx, g_e):
+            rowptr, psi = ctx.saved_tensors
+            g = ctx.basis.tbme_grad(rowptr, psi)
+            g = g * (g_e.reshape(-1, 1) if g_e.dim() else g_e)
+            g = g.to(torch.float32)
+            return (g[0] if ctx.squeeze else g), None, None, None, None, None
+
+    return LowestEigenvalue
+
+
+class _Lazy:
+    fn = None
+
+    def apply(self, *a):
+        if _Lazy.fn is None:
+            _Lazy.fn = _lowest_eigenvalue_function()
+        return _Lazy.fn.apply(*a)
+
+
+_LowestEigenvalue = _Lazy()
 
 
 def build_hamiltonian(basis: Basis, tbme, hbar_omega: float = 20.0, e_sp=None, stream=None):

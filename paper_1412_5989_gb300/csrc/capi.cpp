@@ -366,6 +366,28 @@ int cih_ham_tbme_grad(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, const
     return rc;
 }
 
+int cih_batch_solve(cih_instance_t *inst, int32_t n, double hbar_omega, int32_t nev, int32_t max_iter, double tol,
+                    int64_t hbm_budget, void *stream)
+{
+    if (n < 0 || (n > 0 && !inst)) return fail(CIH_ERR_ARG, "NULL instance array");
+    if (n > 256) return fail(CIH_ERR_UNSUPPORTED, "at most 256 instances per batch");
+    if (nev < 1 || nev > 64 || max_iter < 1 || max_iter > 2048 || !(tol > 0) || hbm_budget < 0)
+        return fail(CIH_ERR_ARG, "nev, max_iter, tol or budget out of range");
+    for (int i = 0; i < n; ++i) {
+        const cih_instance_t &x = inst[i];
+        int rc = needs_device(x.basis);
+        if (rc) return rc;
+        if (x.K < 1 || x.K > 256 || !x.evals_host || (!x.tbme_dev && x.basis->layout.total > 0))
+            return fail(CIH_ERR_ARG, "instance " + std::to_string(i) + ": K, tables or eigenvalue array");
+        if (x.basis->device != inst[0].basis->device)
+            return fail(CIH_ERR_ARG, "instances on different devices");
+    }
+    if (n == 0) return CIH_OK;
+    return guarded([&]() -> int {
+        return batch_solve(inst, n, hbar_omega, nev, max_iter, tol, hbm_budget, (cudaStream_t)stream);
+    });
+}
+
 const char *cih_strerror(int code)
 {
     switch (code) {

@@ -204,6 +204,9 @@ int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
 int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved,
                 const double *esp, int32_t *col, float *val, cudaStream_t st);
 int launch_interleave(int K, int64_t len, const float *in, float *out, cudaStream_t st);
+// one-time set-up of the row kernels a call with K sets would launch (shared-
+// memory limits), so that launches made during a stream capture only launch
+int prepare_rows(const cih_basis &b, int K);
 int launch_grad(const cih_basis &b, const int64_t *rowptr, int K, const double *psi,
                 unsigned long long *acc, cudaStream_t st);
 int launch_grad_finish(int64_t n, const unsigned long long *acc, double *grad, cudaStream_t st);
@@ -222,5 +225,11 @@ void tridiag_eigenvector(int n, const double *d, const double *e, double theta, 
 // Lanczos (lanczos.cu)
 int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val,
             int K, int nev, int max_iter, double tol, double *evals, double *evec0, cudaStream_t st);
+// device bytes lanczos() allocates for a call
+int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter);
+
+// count, admission, build, Lanczos and adjoint of a batch (batch.cpp)
+int batch_solve(cih_instance_t *inst, int n, double hw, int nev, int max_iter, double tol, int64_t budget,
+                cudaStream_t st);
 
 }  // namespace cih

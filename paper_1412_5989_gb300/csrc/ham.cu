@@ -487,7 +487,7 @@ cudaError_t raise_smem_limit(const void *kern, int dev, int bytes)
 
 template <int MODE, int WARPS>
 int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, const FillArgs &F, const GradArgs &G,
-                  cudaStream_t st)
+                  cudaStream_t st, bool dry)
 {
     const DevBasis &D = b.dev;
     const size_t smem = MODE == 0 ? (size_t)sm::S<WARPS> : smem_bytes<WARPS>(D.sp[0].n_orb * D.pn_G);
@@ -497,6 +497,7 @@ int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, co
     auto go = [&](auto kern) -> int {
         cudaError_t ee = raise_smem_limit((const void *)kern, dev, (int)smem);
         if (ee != cudaSuccess) return cuda_fail(ee, "row kernel shared memory");
+        if (dry) return CIH_OK;                              // set-up only, no launch
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
         per_sm = std::max(per_sm, 1);
@@ -516,15 +517,15 @@ int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, co
 
 template <int MODE>
 int launch_rows(const cih_basis &b, const int64_t *rowptr, int64_t *counts, const FillArgs &F, const GradArgs &G,
-                cudaStream_t st)
+                cudaStream_t st, bool dry = false)
 {
     if (b.dim == 0) return CIH_OK;
     const DevBasis &D = b.dev;
     if (D.pn_G > kGroupCap || D.A > kMaxA || D.A - 1 > 32)
         return fail(CIH_ERR_UNSUPPORTED, "more than 33 particles or pn groups above the row kernel's capacity");
     if (D.tbme_len > INT32_MAX) return fail(CIH_ERR_UNSUPPORTED, "two-body table above 2^31 entries");
-    return b.launch_warps == 8 ? launch_rows_w<MODE, 8>(b, rowptr, counts, F, G, st)
-                               : launch_rows_w<MODE, 16>(b, rowptr, counts, F, G, st);
+    return b.launch_warps == 8 ? launch_rows_w<MODE, 8>(b, rowptr, counts, F, G, st, dry)
+                               : launch_rows_w<MODE, 16>(b, rowptr, counts, F, G, st, dry);
 }
 
 // element-major copy of K set-major tables: out[t * K + k] = in[k * len + t]
@@ -560,6 +561,18 @@ int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, con
 {
     FillArgs F{K, hw, tbme, interleaved ? 1 : b.layout.total, interleaved ? (int64_t)K : 1, esp, col, val};
     return launch_rows<1>(b, rowptr, nullptr, F, GradArgs{}, st);
+}
+
+int prepare_rows(const cih_basis &b, int K)
+{
+    FillArgs F{};
+    F.K = K;
+    GradArgs G{};
+    G.K = K;
+    int rc = launch_rows<0>(b, nullptr, nullptr, F, G, nullptr, true);
+    if (!rc) rc = launch_rows<1>(b, nullptr, nullptr, F, G, nullptr, true);
+    if (!rc) rc = launch_rows<2>(b, nullptr, nullptr, F, G, nullptr, true);
+    return rc;
 }
 
 int launch_interleave(int K, int64_t len, const float *in, float *out, cudaStream_t st)

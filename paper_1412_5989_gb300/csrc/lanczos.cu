@@ -229,6 +229,17 @@ int grid_for(int64_t n)
 
 }  // namespace
 
+int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter)
+{
+    const int64_t m = std::min<int64_t>(max_iter, dim);
+    const int64_t nt = std::max<int64_t>(nnz - dim, 1);
+    int64_t bytes = 4 * (dim + 1) + 8 * (dim + 1) + 8 * nt;          // transposed index
+    bytes += 8 * (m + 1) * dim * K + 8 * dim * K;                   // Lanczos vectors, w
+    bytes += 8 * (m + 1) * K * kDotBlocks + 8 * (m + 1) * K + 8 * K; // dot partials, h, scale
+    if (K > 1) bytes += 4 * nnz * K;                                // element-major values
+    return bytes + 8 * 256;                                         // allocation granules
+}
+
 int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val, int K, int nev,
             int max_iter, double tol, double *evals, double *evec0, cudaStream_t st)
 {
