@@ -166,6 +166,22 @@ def oracle_rate(w, rows_n, seed=1):
     return float(cnt.sum()) / dt, int(cnt.sum()), dt, threads, len(rows)
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest value of x over the ranks (replicas report the slowest)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, units_per_step, total_ms):
+    """Units all ranks processed per second: each replica runs `steps` steps of
+    `units_per_step` units; the job takes the slowest rank's time."""
+    return world * steps * units_per_step / (total_ms * 1e-3)
+
+
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args, rank):
@@ -258,13 +274,10 @@ def run_ours(args, rank, world, local_rank):
     launches = cih.kernel_launches() - launches0
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = sum(t_step)
+    total_ms = max_over_ranks(sum(t_step), world, dev)
     if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
         torch.distributed.barrier()
-    value = world * args.steps * nnz / (total_ms * 1e-3)
+    value = whole_job_rate(world, args.steps, nnz, total_ms)
 
     # gradient / forward time ratio: adjoint over the same structure with a
     # normalised vector, against the fill pass
@@ -309,12 +322,8 @@ def run_ours(args, rank, world, local_rank):
             if k >= args.warmup:
                 te.append(a.elapsed_time(b))
             B.close()
-        e_ms = sum(te) / len(te)
-        if world > 1:
-            tt = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        e2e = {"value": world * nnz / (e_ms * 1e-3), "unit": "nnz/s",
+        e_ms = max_over_ranks(sum(te) / len(te), world, dev)
+        e2e = {"value": whole_job_rate(world, 1, nnz, e_ms), "unit": "nnz/s",
                "h2d_bytes_per_step": int(tl * 4),
                "d2h_bytes_per_step": int(nnz * BYTES_PER_NNZ + (dim + 1) * 8)}
         del col_h, val_h
