@@ -10,6 +10,7 @@
 // bucketed by (2M, parity, N) with a stable counting sort, which yields the
 // (2M, N mod 2, N, bits) order in linear time.
 #include <algorithm>
+#include <exception>
 #include <thread>
 #include <climits>
 #include <cstdint>
@@ -182,6 +183,28 @@ void keep_only(Species &s, const std::vector<char> &keep)
     s.M2.resize(k);
 }
 
+// f0() here and f1() on a second thread; an exception of either is rethrown
+template <class F0, class F1>
+void side_by_side(F0 &&f0, F1 &&f1)
+{
+    std::exception_ptr e1;
+    std::thread th([&]() {
+        try {
+            f1();
+        } catch (...) {
+            e1 = std::current_exception();
+        }
+    });
+    try {
+        f0();
+    } catch (...) {
+        th.join();
+        throw;
+    }
+    th.join();
+    if (e1) std::rethrow_exception(e1);
+}
+
 void make_classes(Species &s)
 {
     s.cls.assign(s.n_sd, 0);
@@ -300,7 +323,7 @@ int build_pn_split(cih_basis &b)
 
 }  // namespace
 
-int build_host_basis(const cih_space_t &sp, cih_basis &b)
+int build_host_species(const cih_space_t &sp, cih_basis &b)
 {
     if (sp.Z < 0 || sp.N < 0 || sp.Nmax < 0) return fail(CIH_ERR_ARG, "Z, N and Nmax must be >= 0");
     if (sp.Z > 64 || sp.N > 64) return fail(CIH_ERR_UNSUPPORTED, "more than 64 particles of a species");
@@ -323,12 +346,12 @@ int build_host_basis(const cih_space_t &sp, cih_basis &b)
     b.Nlim = b.N0tot + sp.Nmax;
     int words = 1;
     for (int t = 0; t < 2; ++t) {
-        Species &s = b.s[t];
-        s.Nsub_max = b.Nlim - b.s[1 - t].N0;
-        enumerate_subdets(s);
-        tm.mark(t == 0 ? "enumerate p" : "enumerate n");
-        words = std::max(words, (s.n_orb + 63) / 64);
+        b.s[t].Nsub_max = b.Nlim - b.s[1 - t].N0;
+        words = std::max(words, (b.s[t].n_orb + 63) / 64);
     }
+    // the two species are independent: enumerate them side by side
+    side_by_side([&]() { enumerate_subdets(b.s[0]); }, [&]() { enumerate_subdets(b.s[1]); });
+    tm.mark("enumerate p and n");
     b.W = words <= 1 ? 1 : words <= 2 ? 2 : 4;
     tm.mark("enumerate + bucket sort");
 
@@ -356,8 +379,15 @@ int build_host_basis(const cih_space_t &sp, cih_basis &b)
     }
     // the filter of the second species used the first one's filtered list;
     // pairing is symmetric, so the first species' list is still exact.
-    for (int t = 0; t < 2; ++t) make_classes(b.s[t]);
+    side_by_side([&]() { make_classes(b.s[0]); }, [&]() { make_classes(b.s[1]); });
     tm.mark("appearing filter + classes");
+    return CIH_OK;
+}
+
+int build_host_rest(cih_basis &b)
+{
+    Timer tm("host basis");
+    const cih_space_t &sp = b.space;
 
     // partner ranges: class of (2M - 2M_p, parity of Nlim - N_p), prefix N <= Nlim - N_p
     const Species &P = b.s[0], &Q = b.s[1];
@@ -396,6 +426,12 @@ int build_host_basis(const cih_space_t &sp, cih_basis &b)
     rc = build_pn_split(b);
     tm.mark("pn split");
     return rc;
+}
+
+int build_host_basis(const cih_space_t &sp, cih_basis &b)
+{
+    int rc = build_host_species(sp, b);
+    return rc ? rc : build_host_rest(b);
 }
 
 }  // namespace cih

@@ -135,11 +135,12 @@ int cih_basis_enumerate(const cih_space_t *space, cih_basis_h *out, void *stream
     return guarded([&]() -> int {
         cih_basis *b = new cih_basis;
         Timer tm("basis");
-        int rc = build_host_basis(*space, *b);
-        tm.mark("host tables");
+        int rc = build_host_species(*space, *b);
+        tm.mark("host species");
         if (!rc) {
             cudaError_t e = cudaGetDevice(&b->device);
-            rc = e == cudaSuccess ? upload_and_build_neighbours(*b, (cudaStream_t)stream)
+            rc = e == cudaSuccess ? upload_and_build_neighbours(*b, (cudaStream_t)stream,
+                                                                [b]() { return build_host_rest(*b); })
                                   : cuda_fail(e, "cudaGetDevice");
         }
         if (rc) { release(b); return rc; }

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -194,9 +195,15 @@ int cuda_fail(cudaError_t e, const char *what);
 
 // host basis construction (basis.cpp)
 int build_host_basis(const cih_space_t &sp, cih_basis &b);
+// the same in two parts: orbitals, sub-determinants and classes; then partner
+// ranges, table layout and pn split (which the first device passes do not need)
+int build_host_species(const cih_space_t &sp, cih_basis &b);
+int build_host_rest(cih_basis &b);
 
 // device set-up (neighbours.cu)
-int upload_and_build_neighbours(cih_basis &b, cudaStream_t st);
+// device set-up after build_host_species; host_rest() (build_host_rest) runs
+// while the first device passes are in flight
+int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::function<int()> &host_rest);
 
 // kernels (ham.cu)
 int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st);

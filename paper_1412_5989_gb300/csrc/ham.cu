@@ -80,11 +80,11 @@ __device__ __forceinline__ bool tbme_at(const DevBasis &B, int a, int b, int c, 
 //   A         - n's forward same-class neighbours inside p's partner range:
 //               two-moves from their precomputed table index, one-moves
 //               deferred;
-//   B         - p's candidate records in chunks of 32: lane k reads its
-//               neutron segment from n's bucket directory (plus n itself if
-//               inside q's range), a warp scan places the segments and the
-//               chunk's elements are emitted flattened (lane e writes element
-//               e: contiguous stores).  pp two-moves use the precomputed
+//   B         - p's candidate records in chunks of 64, two per lane: a lane
+//               reads its candidates' neutron segments from n's bucket
+//               directory (plus n itself if inside q's range), a warp scan
+//               places the segments and the chunk's pn elements are emitted
+//               flattened (lane e writes element e: contiguous stores).  pp two-moves use the precomputed
 //               index, pn elements u(a,b) = S[a][kappa] + r(b), proton
 //               one-moves are deferred;
 //   deferred  - one-move elements, lanes over (element, spectator) pairs and
@@ -103,10 +103,8 @@ constexpr int pj = pi + kPairCap;                          // uint8[kPairCap]
 constexpr int warp0 = (pj + kPairCap + 15) / 16 * 16;
 // per warp
 constexpr int w_seg = 0;                                   // int4[64]: colbase, uv, mv, row start
-constexpr int w_incl = w_seg + 64 * 16;                    // int32[64]
-constexpr int w_n1s = w_incl + 256;                        // int32[64]
-constexpr int w_ins = w_n1s + 256;                         // int32[64]
-constexpr int w_spos = w_ins + 256;                       // int32[kSlowCap]
+constexpr int w_ext = w_seg + 64 * 16;                     // int2[64]: list start, insertion point
+constexpr int w_spos = w_ext + 64 * 8;                     // int32[kSlowCap]
 constexpr int w_scol = w_spos + kSlowCap * 4;              // int32[kSlowCap]
 constexpr int w_scode = w_scol + kSlowCap * 4;             // uint32[kSlowCap]
 constexpr int w_occ = w_scode + kSlowCap * 4;              // int16[kMaxA]
@@ -159,8 +157,8 @@ __device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F,
 {
     if (MODE == 1) {
         R.col[e] = (int32_t)colj;
-        if (K1) {
-            const float v = __ldg(F.tbme + (int64_t)idx * F.tb_si);
+        if (K1) {                                                // K = 1: stride 1 in either layout
+            const float v = __ldg(F.tbme + idx);
             R.val[e] = sgn ? -v : v;
         } else {
             for (int k = 0; k < F.K; ++k) {
@@ -266,8 +264,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     const int64_t nnz = MODE == 1 ? rowptr[B.dim] : 0;
     unsigned char *wb = sb + sm::warp0 + wid * sm::w_size;
     int4 *w_seg = sptr<int4>(wb, sm::w_seg);
-    int32_t *w_incl = sptr<int32_t>(wb, sm::w_incl), *w_n1s = sptr<int32_t>(wb, sm::w_n1s);
-    int32_t *w_ins = sptr<int32_t>(wb, sm::w_ins);
+    int2 *w_ext = sptr<int2>(wb, sm::w_ext);
     int32_t *w_spos = sptr<int32_t>(wb, sm::w_spos), *w_scol = sptr<int32_t>(wb, sm::w_scol);
     uint32_t *w_scode = sptr<uint32_t>(wb, sm::w_scode);
     int16_t *w_occ = sptr<int16_t>(wb, sm::w_occ);
@@ -364,23 +361,18 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
             }
         }
 
-        // ---- B: candidates of p in chunks of 64, two per lane (records of the
-        //      next chunk are loaded while the current one is emitted)
+        // ---- B: candidates of p in chunks of 64, two per lane
         const int64_t c0 = B.cand_off[p], c1 = B.cand_off[p + 1];
         const int2 *n1row = B.n1p + SN.n1_off[n];
         const int16_t *dirn = B.dir + (int64_t)n * B.dir_len;
         const int Nn = SN.N[n];
         const int self_rel = B.self_rel[n];
-        int4 rn0 = make_int4(0, 0, 0, 0), rn1 = rn0;
-        int sln0 = 0, sln1 = 0;
-        if (c0 + 2 * lane < c1) { rn0 = B.cand[c0 + 2 * lane]; sln0 = B.cand_self[c0 + 2 * lane]; }
-        if (c0 + 2 * lane + 1 < c1) { rn1 = B.cand[c0 + 2 * lane + 1]; sln1 = B.cand_self[c0 + 2 * lane + 1]; }
         for (int64_t k0 = c0; k0 < c1; k0 += 64) {
-            const int4 r0 = rn0, r1 = rn1;
-            const int sl0 = k0 + 2 * lane < c1 ? sln0 : 0, sl1 = k0 + 2 * lane + 1 < c1 ? sln1 : 0;
             const bool v0 = k0 + 2 * lane < c1, v1 = k0 + 2 * lane + 1 < c1;
-            if (k0 + 64 + 2 * lane < c1) { rn0 = B.cand[k0 + 64 + 2 * lane]; sln0 = B.cand_self[k0 + 64 + 2 * lane]; }
-            if (k0 + 65 + 2 * lane < c1) { rn1 = B.cand[k0 + 65 + 2 * lane]; sln1 = B.cand_self[k0 + 65 + 2 * lane]; }
+            int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
+            int sl0 = 0, sl1 = 0;
+            if (v0) { r0 = B.cand[k0 + 2 * lane]; sl0 = B.cand_self[k0 + 2 * lane]; }
+            if (v1) { r1 = B.cand[k0 + 2 * lane + 1]; sl1 = B.cand_self[k0 + 2 * lane + 1]; }
             // each candidate: pn neutron moves [s_rel, s_rel + lpn) of n's list,
             // plus n itself (a pp two-move or a one-proton move) if inside q's range
             const bool self0 = (sl0 & 0x7F) > Nn, self1 = (sl1 & 0x7F) > Nn;   // 1 + L_q > N_n
@@ -431,34 +423,46 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 }
                 nslow += __popc(m1);
                 if (Tpn > 0) {
-                    // segment table of the 64 candidates: inclusive pn counts, record, list start,
-                    // row start, insertion threshold (INT_MAX if n is not in the range)
+                    // compacted table of the chunk's non-empty pn segments: record, row
+                    // position minus pn start, list start minus pn start, insertion point
+                    const bool ne0 = lpn0 > 0, ne1 = lpn1 > 0;
+                    const unsigned b0 = __ballot_sync(0xffffffffu, ne0), b1 = __ballot_sync(0xffffffffu, ne1);
+                    const int q0 = __popc(b0 & lt) + __popc(b1 & lt), q1 = q0 + (ne0 ? 1 : 0);
                     const int incl_pn = incl & 0xFFFF;
-                    w_incl[2 * lane] = incl_pn - lpn1;
-                    w_incl[2 * lane + 1] = incl_pn;
-                    w_seg[2 * lane] = make_int4(r0.x, r0.z, r0.w, ex0);
-                    w_seg[2 * lane + 1] = make_int4(r1.x, r1.z, r1.w, ex1);
-                    w_n1s[2 * lane] = s0;
-                    w_n1s[2 * lane + 1] = s1;
-                    w_ins[2 * lane] = ins0 >= 0 ? ins0 : INT32_MAX;
-                    w_ins[2 * lane + 1] = ins1 >= 0 ? ins1 : INT32_MAX;
+                    const int st0 = incl_pn - lpn1 - lpn0, st1 = incl_pn - lpn1;     // pn starts
+                    if (ne0) {
+                        w_seg[q0] = make_int4(r0.x, r0.z, r0.w, ex0 - st0);
+                        w_ext[q0] = make_int2(s0 - st0, ins0 >= 0 ? st0 + ins0 : INT32_MAX);
+                    }
+                    if (ne1) {
+                        w_seg[q1] = make_int4(r1.x, r1.z, r1.w, ex1 - st1);
+                        w_ext[q1] = make_int2(s1 - st1, ins1 >= 0 ? st1 + ins1 : INT32_MAX);
+                    }
                     __syncwarp();
+                    // element e belongs to the last non-empty segment starting at or
+                    // before e: per 32-element window, a mask of the segment starts
+                    // inside it (OR over lanes) and the count of earlier starts
+                    const unsigned le = (2u << lane) - 1u;                 // bits 0..lane
+                    int before = 0;                                        // segments started before the window
                     const int iters = (Tpn + 31) >> 5;
                     for (int it = 0; it < iters; ++it) {
-                        const int e = (it << 5) + lane;
+                        const int w0 = it << 5;
+                        unsigned mk = 0;
+                        if (ne0 && st0 >= w0 && st0 < w0 + 32) mk |= 1u << (st0 - w0);
+                        if (ne1 && st1 >= w0 && st1 < w0 + 32) mk |= 1u << (st1 - w0);
+                        mk = __reduce_or_sync(0xffffffffu, mk);
+                        const int e = w0 + lane;
                         if (e < Tpn) {
-                            int j = 0;
-#pragma unroll
-                            for (int step = 32; step > 0; step >>= 1)
-                                if (w_incl[j + step - 1] <= e) j += step;
-                            const int tt = e - (j ? w_incl[j - 1] : 0);
+                            const int j = before + __popc(mk & le) - 1;
                             const int4 sg4 = w_seg[j];
-                            const int at = sg4.w + tt + (tt >= w_ins[j] ? 1 : 0);
-                            const int2 ent = n1row[w_n1s[j] + tt];
+                            const int2 sx = w_ext[j];
+                            const int at = sg4.w + e + (e >= sx.y ? 1 : 0);
+                            const int2 ent = n1row[sx.x + e];
                             int sg;
                             const int idx = pn_index<WARPS>(sb, (uint32_t)sg4.y, (uint32_t)sg4.z, (uint32_t)ent.y, sg);
                             put_single<MODE, K1>(B, F, Gr, R, at, (int64_t)(sg4.x + ent.x), idx, sg);
                         }
+                        before += __popc(mk);
                     }
                     __syncwarp();
                 }

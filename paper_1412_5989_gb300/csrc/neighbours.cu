@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include <functional>
+
 #include "cih_internal.h"
 
 namespace cih {
@@ -642,19 +644,34 @@ int grid_for(int64_t warps)
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * 16));
 }
 
+// Neighbour lists of one species, in three phases so that both species'
+// kernels queue back to back and the host work in between overlaps them:
+//   1. staged forward and one-move passes, their counts scanned, list totals
+//      copied to pinned host memory;
+//   2. (after one synchronisation) exact-size lists: compaction and sort,
+//      later-entry offsets;
+//   3. (once the table layout is on the device) two-move table indices and
+//      the packed neutron move information.
+struct Lists {
+    int64_t n = 0, ns = 0;
+    int64_t *cnt_fw = nullptr, *cnt_n1 = nullptr, *scratch = nullptr, *d_class_stage = nullptr;
+    int32_t *d_cls_of = nullptr, *fw_st = nullptr, *n1_st = nullptr, *fw = nullptr, *n1 = nullptr;
+    int64_t *later = nullptr;
+    int *dmax = nullptr;
+    int cap1 = 1, grid = 1;
+    int64_t *tot = nullptr;                   // pinned: forward and one-move totals
+};
+
 template <int W>
-int build_lists(cih_basis &b, int t, SpeciesBuild &S, cudaStream_t st)
+int lists_phase1(cih_basis &b, int t, SpeciesBuild &S, Lists &L, cudaStream_t st)
 {
-    Timer tm(t == 0 ? "lists p" : "lists n");
-    DevSpecies &D = b.dev.sp[t];
     const Species &hs = b.s[t];
-    const int64_t n = S.n_sd;
-    int64_t *cnt_fw, *cnt_n1, *scratch;
+    const int64_t n = L.n = S.n_sd;
     int rc;
-    if ((rc = dev_alloc(b, &cnt_fw, n + 1)) || (rc = dev_alloc(b, &cnt_n1, n + 1))) return rc;
-    const int64_t ns = scan_scratch_needed(n);
-    if ((rc = dev_alloc(b, &scratch, ns))) return rc;
-    const int grid = grid_for(n);
+    if ((rc = dev_alloc(b, &L.cnt_fw, n + 1)) || (rc = dev_alloc(b, &L.cnt_n1, n + 1))) return rc;
+    L.ns = scan_scratch_needed(n);
+    if ((rc = dev_alloc(b, &L.scratch, L.ns))) return rc;
+    L.grid = grid_for(n);
     // staging: forward lists by class triangle, one-move lists by fixed slots
     std::vector<int32_t> cls_of(std::max<int64_t>(n, 1));
     std::vector<int64_t> class_stage(std::max<size_t>(hs.cls_begin.size(), 1));
@@ -665,92 +682,142 @@ int build_lists(cih_basis &b, int t, SpeciesBuild &S, cudaStream_t st)
         fw_stage += m * (m - 1) / 2;
         for (int64_t x = hs.cls_begin[c]; x < hs.cls_end[c]; ++x) cls_of[x] = (int32_t)c;
     }
-    const int cap1 = std::max(1, hs.Z * std::max(0, hs.n_orb - hs.Z));
-    if (cap1 > kSortTile) return fail(CIH_ERR_UNSUPPORTED, "one-move lists longer than the sort tile");
-    int32_t *d_cls_of, *fw_st, *n1_st;
-    int64_t *d_class_stage;
-    if ((rc = upload(b, &d_cls_of, cls_of, st)) || (rc = upload(b, &d_class_stage, class_stage, st)) ||
-        (rc = dev_alloc(b, &fw_st, fw_stage)) || (rc = dev_alloc(b, &n1_st, (size_t)n * cap1)))
+    L.cap1 = std::max(1, hs.Z * std::max(0, hs.n_orb - hs.Z));
+    if (L.cap1 > kSortTile) return fail(CIH_ERR_UNSUPPORTED, "one-move lists longer than the sort tile");
+    if ((rc = upload(b, &L.d_cls_of, cls_of, st)) || (rc = upload(b, &L.d_class_stage, class_stage, st)) ||
+        (rc = dev_alloc(b, &L.fw_st, fw_stage)) || (rc = dev_alloc(b, &L.n1_st, (size_t)n * L.cap1)))
         return rc;
     if (n > 0) {
         count_launches(2);
-        k_forward_staged<W><<<grid, 256, 0, st>>>(S, d_cls_of, d_class_stage, cnt_fw, fw_st);
-        tm.mark_sync("forward pass", st);
-        k_onemove_staged<W><<<grid, 256, 0, st>>>(S, cap1, cnt_n1, n1_st);
-        tm.mark_sync("one-move pass", st);
+        k_forward_staged<W><<<L.grid, 256, 0, st>>>(S, L.d_cls_of, L.d_class_stage, L.cnt_fw, L.fw_st);
+        k_onemove_staged<W><<<L.grid, 256, 0, st>>>(S, L.cap1, L.cnt_n1, L.n1_st);
     }
-    if ((rc = exclusive_scan_i64(cnt_fw, n, scratch, ns, st))) return rc;
-    if ((rc = exclusive_scan_i64(cnt_n1, n, scratch, ns, st))) return rc;
-    int64_t tot[2];
-    cudaMemcpyAsync(&tot[0], cnt_fw + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&tot[1], cnt_n1 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "neighbour count");
-    tm.mark("scan");
-    int32_t *fw, *n1;
-    if ((rc = dev_alloc(b, &fw, tot[0])) || (rc = dev_alloc(b, &n1, tot[1]))) return rc;
+    if ((rc = exclusive_scan_i64(L.cnt_fw, n, L.scratch, L.ns, st))) return rc;
+    if ((rc = exclusive_scan_i64(L.cnt_n1, n, L.scratch, L.ns, st))) return rc;
+    cudaMemcpyAsync(&L.tot[0], L.cnt_fw + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&L.tot[1], L.cnt_n1 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    return CIH_OK;
+}
+
+int lists_phase2(cih_basis &b, int t, SpeciesBuild &S, Lists &L, cudaStream_t st)
+{
+    const int64_t n = L.n;
+    int rc;
+    if ((rc = dev_alloc(b, &L.fw, L.tot[0])) || (rc = dev_alloc(b, &L.n1, L.tot[1]))) return rc;
     if (n > 0) {
         count_launches(2);
-        k_forward_compact<<<grid, 256, 0, st>>>(S, d_cls_of, d_class_stage, cnt_fw, fw_st, fw);
-        k_onemove_compact_sort<<<(int)std::min<int64_t>(n, 65535), 256, 0, st>>>(n, cap1, cnt_n1, n1_st, n1);
+        k_forward_compact<<<L.grid, 256, 0, st>>>(S, L.d_cls_of, L.d_class_stage, L.cnt_fw, L.fw_st, L.fw);
+        k_onemove_compact_sort<<<(int)std::min<int64_t>(n, 65535), 256, 0, st>>>(n, L.cap1, L.cnt_n1, L.n1_st, L.n1);
     }
-    tm.mark_sync("compact + sort", st);
-    dev_free(b, fw_st);
-    dev_free(b, n1_st);
-    int64_t *later;
-    int *dmax;
-    if ((rc = dev_alloc(b, &later, n)) || (rc = dev_alloc(b, &dmax, 1))) return rc;
-    cudaMemsetAsync(dmax, 0, sizeof(int), st);
+    dev_free(b, L.fw_st);
+    dev_free(b, L.n1_st);
+    L.fw_st = L.n1_st = nullptr;
+    if ((rc = dev_alloc(b, &L.later, n)) || (rc = dev_alloc(b, &L.dmax, 1))) return rc;
+    cudaMemsetAsync(L.dmax, 0, sizeof(int), st);
     if (n > 0) {
         count_launches(1);
-        k_later<<<grid, 256, 0, st>>>(n, S.cls_end, cnt_fw, cnt_n1, n1, later, dmax);
+        k_later<<<L.grid, 256, 0, st>>>(n, S.cls_end, L.cnt_fw, L.cnt_n1, L.n1, L.later, L.dmax);
     }
+    DevSpecies &D = b.dev.sp[t];
+    D.fw_off = L.cnt_fw;
+    D.fw = L.fw;
+    D.n1_off = L.cnt_n1;
+    D.n1 = L.n1;
+    D.n1_later = L.later;
+    return CIH_OK;
+}
+
+template <int W>
+int lists_phase3(cih_basis &b, int t, SpeciesBuild &S, Lists &L, cudaStream_t st)
+{
+    const int64_t n = L.n;
+    int rc;
     int32_t *tb;
-    if ((rc = dev_alloc(b, &tb, tot[0]))) return rc;
+    if ((rc = dev_alloc(b, &tb, L.tot[0]))) return rc;
     if (n > 0) {
         count_launches(1);
-        k_fw_tb<W><<<grid, 256, 0, st>>>(S, t == 0 ? 0 : b.s[0].n_orb, cnt_fw, fw, b.dev.pid, b.dev.gsize,
-                                         b.dev.goff, b.dev.ntot, tb, b.dev_status);
+        k_fw_tb<W><<<L.grid, 256, 0, st>>>(S, t == 0 ? 0 : b.s[0].n_orb, L.cnt_fw, L.fw, b.dev.pid, b.dev.gsize,
+                                           b.dev.goff, b.dev.ntot, tb, b.dev_status);
     }
     if (t == 1) {
         uint32_t *info;
         int32_t *rn;
-        if ((rc = dev_alloc(b, &info, tot[1])) || (rc = upload(b, &rn, b.pn.rn, st))) return rc;
+        if ((rc = dev_alloc(b, &info, L.tot[1])) || (rc = upload(b, &rn, b.pn.rn, st))) return rc;
         if (n > 0) {
             count_launches(1);
-            k_n1_info<W><<<grid, 256, 0, st>>>(S, cnt_n1, n1, rn, info);
+            k_n1_info<W><<<L.grid, 256, 0, st>>>(S, L.cnt_n1, L.n1, rn, info);
         }
         b.dev.n1_info = info;
     }
-    tm.mark_sync("sort + later + two-move + info", st);
-    int mc = 0;
-    e = cudaMemcpyAsync(&mc, dmax, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "neighbour kernels");
-    if (t == 0) b.dev.max_cand = mc;
-    D.fw_off = cnt_fw;
-    D.fw = fw;
-    D.n1_off = cnt_n1;
-    D.n1 = n1;
-    D.n1_later = later;
+    if (t == 0) cudaMemcpyAsync(&L.tot[2], L.dmax, sizeof(int), cudaMemcpyDeviceToHost, st);
     b.dev.fw_tb[t] = tb;
     return CIH_OK;
 }
 
-}  // namespace
+// species t: host arrays, their upload and the one-move hash table
+int species_upload(cih_basis &b, int t, cudaStream_t st)
+{
+    const int W = b.W;
+    const Species &s = b.s[t];
+    int rc;
+    // bit strings compacted to W words
+    std::vector<uint64_t> bits((size_t)s.n_sd * W);
+    for (int64_t i = 0; i < s.n_sd; ++i)
+        for (int w = 0; w < W; ++w) bits[i * W + w] = s.bits[i * kMaxWords + w];
+    std::vector<int8_t> N(s.N.begin(), s.N.end());
+    std::vector<int16_t> M2(s.M2.begin(), s.M2.end());
+    std::vector<int32_t> cls_end(s.n_sd);
+    for (int64_t i = 0; i < s.n_sd; ++i) cls_end[i] = s.cls_end[s.cls[i]];
+    int mabs = 0;
+    for (int m : s.cls_M2) mabs = std::max(mabs, std::abs(m));
+    int mspan = 2 * mabs + 1 + 64;          // room for moves that leave the table
+    int moff = mabs + 32;
+    std::vector<int32_t> lookup((size_t)mspan * 2, -1);
+    for (size_t c = 0; c < s.cls_begin.size(); ++c)
+        lookup[(size_t)(s.cls_M2[c] + moff) * 2 + s.cls_par[c]] = (int32_t)c;
+    std::vector<int32_t> cb(s.cls_begin.begin(), s.cls_begin.end()), ce(s.cls_end.begin(), s.cls_end.end());
+    std::vector<int8_t> oN(s.oN.begin(), s.oN.end());
+    std::vector<int16_t> om2(s.om2.begin(), s.om2.end());
 
-int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
+    uint64_t *d_bits; int8_t *d_N; int16_t *d_M2; int32_t *d_cls_end, *d_lookup, *d_cb, *d_ce;
+    int8_t *d_oN; int16_t *d_om2;
+    if ((rc = upload(b, &d_bits, bits, st)) || (rc = upload(b, &d_N, N, st)) ||
+        (rc = upload(b, &d_M2, M2, st)) || (rc = upload(b, &d_cls_end, cls_end, st)) ||
+        (rc = upload(b, &d_lookup, lookup, st)) || (rc = upload(b, &d_cb, cb, st)) ||
+        (rc = upload(b, &d_ce, ce, st)) || (rc = upload(b, &d_oN, oN, st)) ||
+        (rc = upload(b, &d_om2, om2, st)))
+        return rc;
+    DevSpecies &D = b.dev.sp[t];
+    D.bits = d_bits;
+    D.N = d_N;
+    D.cls_end = d_cls_end;
+    D.n_sd = (int32_t)s.n_sd;
+    D.n_orb = s.n_orb;
+    D.orb_base = t == 0 ? 0 : b.s[0].n_orb;
+
+    SpeciesBuild S{d_bits, d_N, d_M2, d_cls_end, d_lookup, d_cb, d_ce, d_oN, d_om2,
+                   (int32_t)s.n_sd, s.n_orb, moff, mspan, s.Nsub_max, nullptr, 0};
+    uint32_t cap = 64;
+    while (cap < 2 * (uint64_t)s.n_sd) cap <<= 1;
+    int32_t *table;
+    if ((rc = dev_alloc(b, &table, cap))) return rc;
+    if (cudaMemsetAsync(table, 0xFF, sizeof(int32_t) * cap, st) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "hash table");
+    S.hash = table;
+    S.hash_mask = cap - 1;
+    const int hg = (int)std::min<int64_t>((s.n_sd + 255) / 256 + 1, 65535);
+    count_launches(1);
+    if (W == 1) k_hash_build<1><<<hg, 256, 0, st>>>(S, table);
+    else if (W == 2) k_hash_build<2><<<hg, 256, 0, st>>>(S, table);
+    else k_hash_build<4><<<hg, 256, 0, st>>>(S, table);
+    b.sbuild[t] = S;
+    return CIH_OK;
+}
+
+// tables that need the partner ranges, the table layout and the pn split
+int basis_tables_upload(cih_basis &b, cudaStream_t st)
 {
     int rc;
-    int W = b.W;
-    b.stream = st;
-    if ((rc = device_pool(b.device, &b.pool))) return rc;
-    Timer tm("basis device set-up");
-    if ((rc = dev_alloc(b, &b.dev_status, 4))) return rc;
-    b.dev.queue = b.dev_status + 1;
-    if (cudaMemsetAsync(b.dev_status, 0, 4 * sizeof(int), st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "status");
-    // basis-level tables
     int ntot = b.s[0].n_orb + b.s[1].n_orb;
     std::vector<int8_t> orbN(ntot);
     for (int a = 0; a < ntot; ++a) orbN[a] = (int8_t)(a < b.s[0].n_orb ? b.s[0].oN[a] : b.s[1].oN[a - b.s[0].n_orb]);
@@ -773,85 +840,71 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
     b.dev.ntot = ntot;
     b.dev.dim = b.dim;
     b.dev.tbme_len = b.layout.total;
-    tm.mark_sync("basis tables upload", st);
-    {
-        std::vector<int8_t> m2p(std::max(b.s[0].n_orb, 1), 0), Np(std::max(b.s[0].n_orb, 1), 0);
-        for (int a = 0; a < b.s[0].n_orb; ++a) { m2p[a] = (int8_t)b.s[0].om2[a]; Np[a] = (int8_t)b.s[0].oN[a]; }
-        int16_t *d_S; int32_t *d_gs, *d_go; int8_t *d_m2p, *d_Np;
-        if ((rc = upload(b, &d_S, b.pn.S, st)) || (rc = upload(b, &d_gs, b.pn.gsize, st)) ||
-            (rc = upload(b, &d_go, b.pn.goff, st)) || (rc = upload(b, &d_m2p, m2p, st)) ||
-            (rc = upload(b, &d_Np, Np, st)))
-            return rc;
-        b.dev.pn_S = d_S; b.dev.pn_gsize = d_gs; b.dev.pn_goff = d_go; b.dev.m2p = d_m2p; b.dev.Np = d_Np;
-        b.dev.pn_G = b.pn.G;
-        b.dev.pn_m2span = b.pn.m2span;
-    }
+    std::vector<int8_t> m2p(std::max(b.s[0].n_orb, 1), 0), Np(std::max(b.s[0].n_orb, 1), 0);
+    for (int a = 0; a < b.s[0].n_orb; ++a) { m2p[a] = (int8_t)b.s[0].om2[a]; Np[a] = (int8_t)b.s[0].oN[a]; }
+    int16_t *d_S; int32_t *d_gs, *d_go; int8_t *d_m2p, *d_Np;
+    if ((rc = upload(b, &d_S, b.pn.S, st)) || (rc = upload(b, &d_gs, b.pn.gsize, st)) ||
+        (rc = upload(b, &d_go, b.pn.goff, st)) || (rc = upload(b, &d_m2p, m2p, st)) ||
+        (rc = upload(b, &d_Np, Np, st)))
+        return rc;
+    b.dev.pn_S = d_S; b.dev.pn_gsize = d_gs; b.dev.pn_goff = d_go; b.dev.m2p = d_m2p; b.dev.Np = d_Np;
+    b.dev.pn_G = b.pn.G;
+    b.dev.pn_m2span = b.pn.m2span;
+    return CIH_OK;
+}
+
+struct PinnedTotals {
+    int64_t *p = nullptr;
+    ~PinnedTotals() { if (p) cudaFreeHost(p); }
+};
+
+}  // namespace
+
+int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::function<int()> &host_rest)
+{
+    int rc;
+    const int W = b.W;
+    b.stream = st;
+    if ((rc = device_pool(b.device, &b.pool))) return rc;
+    Timer tm("basis device set-up");
+    if ((rc = dev_alloc(b, &b.dev_status, 4))) return rc;
+    b.dev.queue = b.dev_status + 1;
+    if (cudaMemsetAsync(b.dev_status, 0, 4 * sizeof(int), st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "status");
+    PinnedTotals pin;
+    cudaError_t e = cudaMallocHost((void **)&pin.p, 8 * sizeof(int64_t));
+    if (e != cudaSuccess) { pin.p = nullptr; return cuda_fail(e, "pinned totals"); }
+    for (int i = 0; i < 8; ++i) pin.p[i] = 0;
+    Lists L[2];
+    L[0].tot = pin.p;
+    L[1].tot = pin.p + 3;
+    // 1. per species: upload, hash table, staged passes (queued, no synchronisation)
     for (int t = 0; t < 2; ++t) {
-        const Species &s = b.s[t];
-        // bit strings compacted to W words
-        std::vector<uint64_t> bits((size_t)s.n_sd * W);
-        for (int64_t i = 0; i < s.n_sd; ++i)
-            for (int w = 0; w < W; ++w) bits[i * W + w] = s.bits[i * kMaxWords + w];
-        std::vector<int8_t> N(s.N.begin(), s.N.end());
-        std::vector<int16_t> M2(s.M2.begin(), s.M2.end());
-        std::vector<int32_t> cls_end(s.n_sd);
-        for (int64_t i = 0; i < s.n_sd; ++i) cls_end[i] = s.cls_end[s.cls[i]];
-        int mabs = 0;
-        for (int m : s.cls_M2) mabs = std::max(mabs, std::abs(m));
-        int mspan = 2 * mabs + 1 + 64;          // room for moves that leave the table
-        int moff = mabs + 32;
-        std::vector<int32_t> lookup((size_t)mspan * 2, -1);
-        for (size_t c = 0; c < s.cls_begin.size(); ++c)
-            lookup[(size_t)(s.cls_M2[c] + moff) * 2 + s.cls_par[c]] = (int32_t)c;
-        std::vector<int32_t> cb(s.cls_begin.begin(), s.cls_begin.end()), ce(s.cls_end.begin(), s.cls_end.end());
-        std::vector<int8_t> oN(s.oN.begin(), s.oN.end());
-        std::vector<int16_t> om2(s.om2.begin(), s.om2.end());
-        tm.mark_sync(t == 0 ? "species p host prep" : "species n host prep", st);
-
-        uint64_t *d_bits; int8_t *d_N; int16_t *d_M2; int32_t *d_cls_end, *d_lookup, *d_cb, *d_ce;
-        int8_t *d_oN; int16_t *d_om2;
-        if ((rc = upload(b, &d_bits, bits, st)) || (rc = upload(b, &d_N, N, st)) ||
-            (rc = upload(b, &d_M2, M2, st)) || (rc = upload(b, &d_cls_end, cls_end, st)) ||
-            (rc = upload(b, &d_lookup, lookup, st)) || (rc = upload(b, &d_cb, cb, st)) ||
-            (rc = upload(b, &d_ce, ce, st)) || (rc = upload(b, &d_oN, oN, st)) ||
-            (rc = upload(b, &d_om2, om2, st)))
-            return rc;
-        DevSpecies &D = b.dev.sp[t];
-        D.bits = d_bits;
-        D.N = d_N;
-        D.cls_end = d_cls_end;
-        D.n_sd = (int32_t)s.n_sd;
-        D.n_orb = s.n_orb;
-        D.orb_base = t == 0 ? 0 : b.s[0].n_orb;
-
-        SpeciesBuild S{d_bits, d_N, d_M2, d_cls_end, d_lookup, d_cb, d_ce, d_oN, d_om2,
-                       (int32_t)s.n_sd, s.n_orb, moff, mspan, s.Nsub_max, nullptr, 0};
-        {
-            uint32_t cap = 64;
-            while (cap < 2 * (uint64_t)s.n_sd) cap <<= 1;
-            int32_t *table;
-            if ((rc = dev_alloc(b, &table, cap))) return rc;
-            if (cudaMemsetAsync(table, 0xFF, sizeof(int32_t) * cap, st) != cudaSuccess)
-                return cuda_fail(cudaGetLastError(), "hash table");
-            S.hash = table;
-            S.hash_mask = cap - 1;
-            const int hg = (int)std::min<int64_t>((s.n_sd + 255) / 256 + 1, 65535);
-            count_launches(1);
-            if (W == 1) k_hash_build<1><<<hg, 256, 0, st>>>(S, table);
-            else if (W == 2) k_hash_build<2><<<hg, 256, 0, st>>>(S, table);
-            else k_hash_build<4><<<hg, 256, 0, st>>>(S, table);
-        }
-        b.sbuild[t] = S;
-        tm.mark_sync(t == 0 ? "species p upload" : "species n upload", st);
-        if (W == 1) rc = build_lists<1>(b, t, S, st);
-        else if (W == 2) rc = build_lists<2>(b, t, S, st);
-        else rc = build_lists<4>(b, t, S, st);
+        if ((rc = species_upload(b, t, st))) return rc;
+        if (W == 1) rc = lists_phase1<1>(b, t, b.sbuild[t], L[t], st);
+        else if (W == 2) rc = lists_phase1<2>(b, t, b.sbuild[t], L[t], st);
+        else rc = lists_phase1<4>(b, t, b.sbuild[t], L[t], st);
         if (rc) return rc;
-        tm.mark_sync(t == 0 ? "species p lists" : "species n lists", st);
+    }
+    tm.mark("species queued");
+    // host work that the kernels above do not need: ranges, table layout, pn split
+    if ((rc = host_rest())) return rc;
+    tm.mark("host ranges + layout");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "neighbour counts");
+    tm.mark("staged passes done");
+    // 2. exact-size lists
+    for (int t = 0; t < 2; ++t)
+        if ((rc = lists_phase2(b, t, b.sbuild[t], L[t], st))) return rc;
+    // 3. basis tables, two-move indices, neutron move information
+    if ((rc = basis_tables_upload(b, st))) return rc;
+    for (int t = 0; t < 2; ++t) {
+        if (W == 1) rc = lists_phase3<1>(b, t, b.sbuild[t], L[t], st);
+        else if (W == 2) rc = lists_phase3<2>(b, t, b.sbuild[t], L[t], st);
+        else rc = lists_phase3<4>(b, t, b.sbuild[t], L[t], st);
+        if (rc) return rc;
     }
     b.scan_scratch_len = scan_scratch_needed(b.dim);
     if ((rc = dev_alloc(b, &b.scan_scratch, b.scan_scratch_len))) return rc;
-    tm.mark_sync("scratch", st);
     {
         // neutron one-move lists: packed entries and bucket directory
         const Species &Q = b.s[1];
@@ -862,10 +915,7 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
         const int dir_len = 1 + RC * NL;
         if (dir_len > 65535) return fail(CIH_ERR_UNSUPPORTED, "neutron bucket directory too long");
         const int64_t nn = Q.n_sd;
-        int64_t tot = 0;
-        cudaError_t e = cudaMemcpyAsync(&tot, b.dev.sp[1].n1_off + nn, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(e, "one-move list size");
+        const int64_t tot = L[1].tot[1];
         int2 *n1p;
         int16_t *dir;
         if ((rc = dev_alloc(b, &n1p, tot)) || (rc = dev_alloc(b, &dir, (size_t)nn * dir_len))) return rc;
@@ -893,7 +943,6 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
             k_occ<4><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
             k_occ<4><<<g1, 256, 0, st>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
         }
-        tm.mark_sync("directory + occupied lists", st);
         b.dev.self_rel = srel;
         b.dev.occ[0] = occp;
         b.dev.occ[1] = occn;
@@ -903,6 +952,7 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
         b.dev.NL = NL;
         b.dev.DM = dm;
     }
+    tm.mark("directory + occupied lists queued");
     {
         const int64_t np = b.s[0].n_sd;
         int64_t *coff;
@@ -914,10 +964,11 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
             k_cand_count<<<grid, 256, 0, st>>>(np, b.dev.sp[0].fw_off, b.dev.sp[0].n1_off, b.dev.sp[0].n1_later, coff);
         }
         if ((rc = exclusive_scan_i64(coff, np, b.scan_scratch, b.scan_scratch_len, st))) return rc;
-        int64_t total = 0;
-        cudaError_t e = cudaMemcpyAsync(&total, coff + np, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        int64_t *total_p = pin.p + 6;
+        e = cudaMemcpyAsync(total_p, coff + np, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "candidate count");
+        const int64_t total = *total_p;
         int4 *cand;
         uint8_t *cself;
         if ((rc = dev_alloc(b, &cand, total)) || (rc = dev_alloc(b, &cself, total))) return rc;
@@ -929,7 +980,7 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
             else k_cand<4><<<grid, 256, 0, st>>>(SB, b.dev, SB.N, SB.M2, b.Nlim, coff, cand, cself);
             k_row_p<<<grid, 256, 0, st>>>(np, b.dev.rowbase, row_p);
         }
-        tm.mark_sync("candidate table", st);
+        tm.mark("candidate table queued");
         b.dev.cand_off = coff;
         b.dev.cand = cand;
         b.dev.cand_self = cself;
@@ -938,8 +989,9 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st)
         b.dev.nZ[0] = b.space.Z;
         b.dev.nZ[1] = b.space.N;
     }
-    cudaError_t e = cudaStreamSynchronize(st);
+    e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "basis upload");
+    b.dev.max_cand = (int32_t)L[0].tot[2];
     return CIH_OK;
 }
 
