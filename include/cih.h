@@ -148,6 +148,18 @@ int cih_ham_fill_interleaved(cih_basis_h h, const int64_t *rowptr_dev, int32_t K
                              const float *tbme_il_dev, const double *e_sp_dev,
                              int32_t *col_dev, float *val_dev, void *stream);
 
+/* The batched fill: K interleaved tables in (tbme_il_dev[t * K + k], as from
+ * cih_tbme_interleave) and the values out element-major: val_em_dev[e * K +
+ * k] is the value of stored nonzero e in set k (nnz x K float, device,
+ * caller-owned), so each nonzero's K values are one contiguous write.  This
+ * is the layout cih_lanczos_lowest_em reads.  Columns as cih_ham_fill.
+ * Multi-term values (diagonal, one-particle moves) are summed per set in term
+ * order, so they can differ from the K = 1 fill in the last bit; single-term
+ * values are identical.  Errors as cih_ham_fill. */
+int cih_ham_fill_batched(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,
+                         const float *tbme_il_dev, const double *e_sp_dev, int32_t *col_dev, float *val_em_dev,
+                         void *stream);
+
 /* tbme_il_dev[t * K + k] = tbme_dev[k * tbme_len + t] (device arrays, caller-
  * owned, stream-ordered).  Errors: CIH_ERR_ARG, CIH_ERR_CUDA. */
 int cih_tbme_interleave(int32_t K, int64_t tbme_len, const float *tbme_dev, float *tbme_il_dev, void *stream);
@@ -157,8 +169,9 @@ int cih_tbme_interleave(int32_t K, int64_t tbme_len, const float *tbme_dev, floa
  * Errors: CIH_ERR_ARG. */
 int cih_set_launch(cih_basis_h h, int32_t warps_per_cta, int32_t ctas_per_sm);
 
-/* Autotuner: times the fill (cih_ham_fill, or cih_ham_fill_interleaved when
- * interleaved != 0, same arguments) for every launch shape -- warps per CTA in
+/* Autotuner: times the fill (cih_ham_fill; cih_ham_fill_interleaved when
+ * interleaved == 1; cih_ham_fill_batched when interleaved == 2; same
+ * arguments) for every launch shape -- warps per CTA in
  * {16, 8} x CTAs per SM in {as many as fit, 1, 2, 3} -- with CUDA events
  * (best of two after one warm-up), keeps the fastest on the handle and reports
  * it.  The outputs col_dev / val_dev are written (with the final, correct
@@ -190,6 +203,13 @@ int cih_autotune_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, doubl
 int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
                        const float *val_dev, int32_t K, int32_t nev, int32_t max_iter,
                        double tol, double *evals_host, double *evec0_dev, void *stream);
+
+/* As cih_lanczos_lowest with the values element-major (val_em_dev[e * K + k],
+ * the output of cih_ham_fill_batched), which the matrix-vector products read
+ * directly: no element-major copy is made. */
+int cih_lanczos_lowest_em(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
+                          const float *val_em_dev, int32_t K, int32_t nev, int32_t max_iter,
+                          double tol, double *evals_host, double *evec0_dev, void *stream);
 
 /* Adjoint: d E0 / d t for every two-body table entry t of each of K sets,
  * given the normalised lowest eigenvectors psi (Hellmann-Feynman, E0 =

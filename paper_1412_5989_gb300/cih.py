@@ -46,6 +46,7 @@ _SIGS = {
     "cih_ham_count": [_P, _P, _i64p, _P],
     "cih_ham_fill": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
     "cih_ham_fill_interleaved": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
+    "cih_ham_fill_batched": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
     "cih_tbme_interleave": [C.c_int32, C.c_int64, _P, _P, _P],
     "cih_set_launch": [_P, C.c_int32, C.c_int32],
     "cih_autotune_fill": [_P, _P, C.c_int32, C.c_double, _P, C.c_int32, _P, _P, _P, _P,
@@ -53,6 +54,7 @@ _SIGS = {
     "cih_check": [_P, _P],
     "cih_batch_solve": [C.POINTER(Instance), C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int64, _P],
     "cih_lanczos_lowest": [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _P, _P],
+    "cih_lanczos_lowest_em": [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _P, _P],
     "cih_ham_tbme_grad": [_P, _P, C.c_int32, _P, _P, _P],
     "cih_tridiag_eigen": [C.c_int32, _dp, _dp, _dp, _dp],
     "cih_kernel_launches": [_i64p],
@@ -252,17 +254,36 @@ class Basis:
                                          _ptr(e_sp), _ptr(col), _ptr(val), _stream(stream)), "ham_fill_interleaved")
         return col[:nnz], val[:, :nnz]
 
+    def fill_batched(self, rowptr, nnz: int, tbme_il, K: int, hbar_omega: float = 20.0, e_sp=None,
+                     stream=None, col=None, val=None):
+        """Batched fill: K element-major tables (tbme_interleave's output) in,
+        element-major values out.  Returns (col int32[nnz], val float32[nnz, K])."""
+        import torch
+        if tbme_il.dtype != torch.float32 or not tbme_il.is_cuda or tbme_il.numel() != K * self.tbme_len:
+            raise ValueError("tbme_il must be a float32 CUDA tensor of K * tbme_len entries")
+        if col is None:
+            col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        if val is None:
+            val = torch.empty((max(nnz, 1), K), dtype=torch.float32, device="cuda")
+        if e_sp is not None:
+            e_sp = e_sp.to(device="cuda", dtype=torch.float64).contiguous()
+        _ok(lib.cih_ham_fill_batched(self._h, _ptr(rowptr), K, float(hbar_omega), _ptr(tbme_il.contiguous()),
+                                     _ptr(e_sp), _ptr(col), _ptr(val), _stream(stream)), "ham_fill_batched")
+        return col[:nnz], val[:nnz]
+
     def set_launch(self, warps_per_cta: int, ctas_per_sm: int = 0):
         """Launch shape of this basis' row kernels."""
         _ok(lib.cih_set_launch(self._h, warps_per_cta, ctas_per_sm), "set_launch")
 
     def autotune_fill(self, rowptr, nnz: int, tbme, hbar_omega: float = 20.0, e_sp=None, *, K: int | None = None,
-                      interleaved: bool = False, stream=None, col=None, val=None):
+                      interleaved: bool = False, batched: bool = False, stream=None, col=None, val=None):
         """Time every launch shape of the fill and keep the fastest on this basis.
         tbme: (K, tbme_len) tables, or with interleaved=True the element-major
-        copy from tbme_interleave (then K must be given).  Returns
-        (col, val, (warps_per_cta, ctas_per_sm, ms))."""
+        copy from tbme_interleave (then K must be given); batched=True times
+        the batched fill (interleaved tables, element-major values (nnz, K)).
+        Returns (col, val, (warps_per_cta, ctas_per_sm, ms))."""
         import torch
+        interleaved = interleaved or batched
         if interleaved:
             if K is None or tbme.numel() != K * self.tbme_len:
                 raise ValueError("interleaved tables need K and K * tbme_len entries")
@@ -270,29 +291,36 @@ class Basis:
         else:
             t = self._check_table(tbme)
             K = t.shape[0]
+        if batched and val is None:
+            val = torch.empty((max(nnz, 1), K), dtype=torch.float32, device="cuda")
         col, val = self._outputs(nnz, K, col, val)
         if e_sp is not None:
             e_sp = e_sp.to(device="cuda", dtype=torch.float64).contiguous()
         w, c, ms = C.c_int32(), C.c_int32(), C.c_float()
-        _ok(lib.cih_autotune_fill(self._h, _ptr(rowptr), K, float(hbar_omega), _ptr(t), int(interleaved),
+        mode = 2 if batched else int(interleaved)
+        _ok(lib.cih_autotune_fill(self._h, _ptr(rowptr), K, float(hbar_omega), _ptr(t), mode,
                                   _ptr(e_sp), _ptr(col), _ptr(val), _stream(stream), C.byref(w), C.byref(c),
                                   C.byref(ms)), "autotune_fill")
-        return col[:nnz], val[:, :nnz], (w.value, c.value, ms.value)
+        v = val[:nnz] if batched else val[:, :nnz]
+        return col[:nnz], v, (w.value, c.value, ms.value)
 
     def check(self, stream=None):
         _ok(lib.cih_check(self._h, _stream(stream)), "check")
 
     def lanczos(self, rowptr, col, val, nev: int = 5, max_iter: int = 300, tol: float = 1e-8,
-                want_vectors: bool = True, stream=None):
-        """Lowest nev eigenvalues of each of the K matrices; returns
-        (evals (K, nev) float64 numpy, evec0 (K, dim) float64 CUDA or None, converged)."""
+                want_vectors: bool = True, stream=None, element_major: bool = False):
+        """Lowest nev eigenvalues of each of the K matrices; val is (K, nnz)
+        set-major, or (nnz, K) element-major with element_major=True (the
+        batched fill's output).  Returns (evals (K, nev) float64 numpy,
+        evec0 (K, dim) float64 CUDA or None, converged)."""
         import torch
         v = (val if val.dim() == 2 else val.unsqueeze(0)).contiguous()
-        K = v.shape[0]
+        K = v.shape[1] if element_major else v.shape[0]
         ev = np.zeros((K, nev))
         vec = torch.empty((K, self.dim), dtype=torch.float64, device="cuda") if want_vectors else None
-        rc = _ok(lib.cih_lanczos_lowest(self._h, _ptr(rowptr), _ptr(col), _ptr(v), K, nev, max_iter, tol,
-                                        ev.ctypes.data_as(_dp), _ptr(vec), _stream(stream)), "lanczos_lowest")
+        fn = lib.cih_lanczos_lowest_em if element_major else lib.cih_lanczos_lowest
+        rc = _ok(fn(self._h, _ptr(rowptr), _ptr(col), _ptr(v), K, nev, max_iter, tol,
+                    ev.ctypes.data_as(_dp), _ptr(vec), _stream(stream)), "lanczos_lowest")
         return ev, vec, rc == 0
 
     def tbme_grad(self, rowptr, psi, stream=None):

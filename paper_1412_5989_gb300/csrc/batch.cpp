@@ -213,7 +213,7 @@ int batch_solve(cih_instance_t *inst, int n, double hw, int nev, int max_iter, d
                 return fail(CIH_ERR_NOMEM, "batch: wave arrays");
         }
         rc = fan_out(st, w, br, true, [&](int i, cudaStream_t s) {
-            return launch_fill(*inst[i].basis, rowptr[i], inst[i].K, hw, inst[i].tbme_dev, false, inst[i].e_sp_dev,
+            return launch_fill(*inst[i].basis, rowptr[i], inst[i].K, hw, inst[i].tbme_dev, false, false, inst[i].e_sp_dev,
                                col[i], val[i], s);
         });
         if (rc) return rc;

@@ -240,7 +240,8 @@ int cih_ham_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hba
     if (rc) return rc;
     if (!rowptr_dev || !col_dev || !val_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
     if (!tbme_dev && h->layout.total > 0) return fail(CIH_ERR_ARG, "NULL two-body table");
-    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, false, e_sp_dev, col_dev, val_dev, (cudaStream_t)stream);
+    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, false, false, e_sp_dev, col_dev, val_dev,
+                       (cudaStream_t)stream);
 }
 
 int cih_ham_fill_interleaved(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,
@@ -251,7 +252,19 @@ int cih_ham_fill_interleaved(cih_basis_h h, const int64_t *rowptr_dev, int32_t K
     if (rc) return rc;
     if (!rowptr_dev || !col_dev || !val_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
     if (!tbme_il_dev && h->layout.total > 0) return fail(CIH_ERR_ARG, "NULL two-body table");
-    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_il_dev, true, e_sp_dev, col_dev, val_dev,
+    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_il_dev, true, false, e_sp_dev, col_dev, val_dev,
+                       (cudaStream_t)stream);
+}
+
+int cih_ham_fill_batched(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,
+                         const float *tbme_il_dev, const double *e_sp_dev, int32_t *col_dev, float *val_em_dev,
+                         void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!rowptr_dev || !col_dev || !val_em_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
+    if (!tbme_il_dev && h->layout.total > 0) return fail(CIH_ERR_ARG, "NULL two-body table");
+    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_il_dev, true, true, e_sp_dev, col_dev, val_em_dev,
                        (cudaStream_t)stream);
 }
 
@@ -294,7 +307,8 @@ int cih_autotune_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, doubl
             float ms = 0.0f, tmin = 1e30f;
             for (int rep = 0; rep < 3 && !rc; ++rep) {
                 cudaEventRecord(e0, st);
-                rc = launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, interleaved != 0, e_sp_dev, col_dev, val_dev, st);
+                rc = launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, interleaved != 0, interleaved == 2, e_sp_dev,
+                                 col_dev, val_dev, st);
                 cudaEventRecord(e1, st);
                 if (!rc && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
                     rep > 0)
@@ -332,9 +346,9 @@ int cih_check(cih_basis_h h, void *stream)
     return CIH_OK;
 }
 
-int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
-                       const float *val_dev, int32_t K, int32_t nev, int32_t max_iter, double tol,
-                       double *evals_host, double *evec0_dev, void *stream)
+static int lanczos_entry(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev, const float *val_dev,
+                         int32_t K, int32_t nev, int32_t max_iter, double tol, double *evals_host,
+                         double *evec0_dev, void *stream, bool values_em)
 {
     int rc = needs_device(h);
     if (rc) return rc;
@@ -343,8 +357,23 @@ int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *
         return fail(CIH_ERR_ARG, "K, nev, max_iter or tol out of range");
     return guarded([&]() -> int {
         return lanczos(*h, rowptr_dev, col_dev, val_dev, K, nev, max_iter, tol, evals_host, evec0_dev,
-                       (cudaStream_t)stream);
+                       (cudaStream_t)stream, values_em);
     });
+}
+
+int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
+                       const float *val_dev, int32_t K, int32_t nev, int32_t max_iter, double tol,
+                       double *evals_host, double *evec0_dev, void *stream)
+{
+    return lanczos_entry(h, rowptr_dev, col_dev, val_dev, K, nev, max_iter, tol, evals_host, evec0_dev, stream, false);
+}
+
+int cih_lanczos_lowest_em(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
+                          const float *val_em_dev, int32_t K, int32_t nev, int32_t max_iter, double tol,
+                          double *evals_host, double *evec0_dev, void *stream)
+{
+    return lanczos_entry(h, rowptr_dev, col_dev, val_em_dev, K, nev, max_iter, tol, evals_host, evec0_dev, stream,
+                         true);
 }
 
 int cih_ham_tbme_grad(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, const double *psi_dev,

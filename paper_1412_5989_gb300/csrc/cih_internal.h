@@ -208,7 +208,8 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
 // kernels (ham.cu)
 int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
 int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
-int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved,
+// interleaved: tables element-major (len x K); em: values element-major (nnz x K)
+int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved, bool em,
                 const double *esp, int32_t *col, float *val, cudaStream_t st);
 int launch_interleave(int K, int64_t len, const float *in, float *out, cudaStream_t st);
 // one-time set-up of the row kernels a call with K sets would launch (shared-
@@ -231,7 +232,8 @@ void tridiag_eigenvector(int n, const double *d, const double *e, double theta, 
 
 // Lanczos (lanczos.cu)
 int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val,
-            int K, int nev, int max_iter, double tol, double *evals, double *evec0, cudaStream_t st);
+            int K, int nev, int max_iter, double tol, double *evals, double *evec0, cudaStream_t st,
+            bool values_em = false);
 // device bytes lanczos() allocates for a call
 int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter);
 

@@ -39,6 +39,9 @@ struct FillArgs {
     double hw;
     const float *tbme;
     int64_t tb_sk, tb_si;
+    int vec4;                 // interleaved, K % 4 == 0, 16-byte aligned: float4 table reads (and
+                              // float4 value writes when em)
+    int em;                   // values element-major: val[e * K + k] (else set-major val[k * nnz + e])
     const double *esp;        // combined orbital energies or null
     int32_t *col;
     float *val;               // K x nnz
@@ -91,6 +94,7 @@ __device__ __forceinline__ bool tbme_at(const DevBasis &B, int a, int b, int c, 
 //               a segmented FP64 reduction.
 
 constexpr int kGroupCap = 128;
+constexpr int kLaneSets = 16;     // from this many sets on, multi-term sums run with lanes over sets
 constexpr int kSlowCap = 64;
 constexpr int kMaxA = 64;
 constexpr int kPairCap = kMaxA * (kMaxA - 1) / 2;
@@ -107,8 +111,8 @@ constexpr int w_ext = w_seg + 64 * 16;                     // int2[64]: list sta
 constexpr int w_spos = w_ext + 64 * 8;                     // int32[kSlowCap]
 constexpr int w_scol = w_spos + kSlowCap * 4;              // int32[kSlowCap]
 constexpr int w_scode = w_scol + kSlowCap * 4;             // uint32[kSlowCap]
-constexpr int w_occ = w_scode + kSlowCap * 4;              // int16[kMaxA]
-constexpr int w_size = (w_occ + kMaxA * 2 + 15) / 16 * 16;
+constexpr int w_occ = w_scode + kSlowCap * 4;              // int16[kMaxA], then int2[32]: spectator entries
+constexpr int w_size = (w_occ + kMaxA * 2 + 32 * 8 + 15) / 16 * 16;
 // the pn split table S (int16[n_orb_p * G]) follows the per-warp areas
 template <int WARPS>
 constexpr int S = warp0 + WARPS * w_size;
@@ -142,11 +146,12 @@ __device__ __forceinline__ int pn_index(const unsigned char *sb, uint32_t uv, ui
     return go[kappa] + u * gs[kappa] - ((u * (u - 1)) >> 1) + (v - u);
 }
 
-// Row output view: column and value pointers at the row's first element.
+// Row output view: column and value pointers at the row's first element;
+// the value of set k at row position e is val[e * es + k * ks].
 struct RowOut {
     int32_t *col;
     float *val;
-    int64_t nnz;      // value set stride
+    int64_t es, ks;
     int64_t row;
 };
 
@@ -161,9 +166,54 @@ __device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F,
             const float v = __ldg(F.tbme + idx);
             R.val[e] = sgn ? -v : v;
         } else {
-            for (int k = 0; k < F.K; ++k) {
-                const float v = __ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)idx * F.tb_si);
-                R.val[(int64_t)k * R.nnz + e] = sgn ? -v : v;
+            // K sets: the value of set k goes to val[e * es + k * ks]; the sign flips bit 31
+            const float *t = F.tbme + (int64_t)idx * F.tb_si;
+            const int sm = sgn ? (int)0x80000000 : 0;
+            if (F.em) {                                          // the K values of e are contiguous
+                float *o = R.val + (int64_t)e * R.es;
+                if (F.vec4) {
+                    const float4 *t4 = reinterpret_cast<const float4 *>(t);
+                    float4 *o4 = reinterpret_cast<float4 *>(o);
+#pragma unroll 4
+                    for (int k4 = 0; k4 < (F.K >> 2); ++k4) {
+                        float4 v = __ldg(t4 + k4);
+                        v.x = __int_as_float(__float_as_int(v.x) ^ sm);
+                        v.y = __int_as_float(__float_as_int(v.y) ^ sm);
+                        v.z = __int_as_float(__float_as_int(v.z) ^ sm);
+                        v.w = __int_as_float(__float_as_int(v.w) ^ sm);
+                        o4[k4] = v;
+                    }
+                } else {
+                    for (int k = 0; k < F.K; ++k) o[k] = __int_as_float(__float_as_int(__ldg(t + k * F.tb_sk)) ^ sm);
+                }
+                return;
+            }
+            float *out = R.val + e;
+            const int64_t vs = R.ks;
+            if (F.vec4) {                                        // the K values of idx are contiguous
+                const float4 *t4 = reinterpret_cast<const float4 *>(t);
+#pragma unroll 4
+                for (int k4 = 0; k4 < (F.K >> 2); ++k4) {
+                    const float4 v = __ldg(t4 + k4);
+                    float *o = out + (int64_t)(4 * k4) * vs;
+                    o[0] = __int_as_float(__float_as_int(v.x) ^ sm);
+                    o[vs] = __int_as_float(__float_as_int(v.y) ^ sm);
+                    o[2 * vs] = __int_as_float(__float_as_int(v.z) ^ sm);
+                    o[3 * vs] = __int_as_float(__float_as_int(v.w) ^ sm);
+                }
+            } else {
+                const int64_t sk = F.tb_sk;
+                int k = 0;
+                for (; k + 4 <= F.K; k += 4) {                   // four independent reads in flight
+                    const float v0 = __ldg(t + k * sk), v1 = __ldg(t + (k + 1) * sk);
+                    const float v2 = __ldg(t + (k + 2) * sk), v3 = __ldg(t + (k + 3) * sk);
+                    float *o = out + (int64_t)k * vs;
+                    o[0] = __int_as_float(__float_as_int(v0) ^ sm);
+                    o[vs] = __int_as_float(__float_as_int(v1) ^ sm);
+                    o[2 * vs] = __int_as_float(__float_as_int(v2) ^ sm);
+                    o[3 * vs] = __int_as_float(__float_as_int(v3) ^ sm);
+                }
+                for (; k < F.K; ++k) out[(int64_t)k * vs] = __int_as_float(__float_as_int(__ldg(t + k * sk)) ^ sm);
             }
         }
     } else if (MODE == 2) {
@@ -172,6 +222,56 @@ __device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F,
             const double f = 2.0 * psi[R.row] * psi[colj];
             const long long qv = __double2ll_rn((sgn ? -f : f) * kFixScale);
             atomicAdd(Gr.acc + (int64_t)k * B.tbme_len + idx, (unsigned long long)qv);
+        }
+    }
+}
+
+// Element-major K-set values of up to 32 single-term elements, one per lane
+// (act, table index idx, sign bit sgn, row position e), written by the whole
+// warp: K/4 lanes copy one element's K values as float4s, so that a store
+// instruction covers whole lines.  Needs F.em, F.vec4 and K/4 dividing 32 or
+// a multiple of 32.  Columns are written by the caller.
+__device__ __forceinline__ void put_values_coop(const FillArgs &F, const RowOut &R, bool act, int idx, int sgn, int e)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned am = __ballot_sync(0xffffffffu, act);
+    if (!am) return;
+    const int L = F.K >> 2;                                      // float4s per element
+    const int last = 31 - __clz(am);
+    if (L <= 32) {
+        const int P = 32 / L, sub = lane / L, q = lane % L;
+        for (int j0 = 0; j0 <= last; j0 += P) {
+            const int src = j0 + sub;
+            const int jidx = __shfl_sync(0xffffffffu, idx, src & 31);
+            const int je = __shfl_sync(0xffffffffu, e, src & 31);
+            const int js = __shfl_sync(0xffffffffu, sgn, src & 31);
+            if (src < 32 && ((am >> src) & 1)) {
+                const int sm = js ? (int)0x80000000 : 0;
+                float4 v = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)jidx * F.K) + q);
+                v.x = __int_as_float(__float_as_int(v.x) ^ sm);
+                v.y = __int_as_float(__float_as_int(v.y) ^ sm);
+                v.z = __int_as_float(__float_as_int(v.z) ^ sm);
+                v.w = __int_as_float(__float_as_int(v.w) ^ sm);
+                reinterpret_cast<float4 *>(R.val + (int64_t)je * R.es)[q] = v;
+            }
+        }
+    } else {
+        for (int j = 0; j <= last; ++j) {
+            const int jidx = __shfl_sync(0xffffffffu, idx, j);
+            const int je = __shfl_sync(0xffffffffu, e, j);
+            const int js = __shfl_sync(0xffffffffu, sgn, j);
+            if (!((am >> j) & 1)) continue;
+            const int sm = js ? (int)0x80000000 : 0;
+            const float4 *t4 = reinterpret_cast<const float4 *>(F.tbme + (int64_t)jidx * F.K);
+            float4 *o4 = reinterpret_cast<float4 *>(R.val + (int64_t)je * R.es);
+            for (int q = lane; q < L; q += 32) {
+                float4 v = __ldg(t4 + q);
+                v.x = __int_as_float(__float_as_int(v.x) ^ sm);
+                v.y = __int_as_float(__float_as_int(v.y) ^ sm);
+                v.z = __int_as_float(__float_as_int(v.z) ^ sm);
+                v.w = __int_as_float(__float_as_int(v.w) ^ sm);
+                o4[q] = v;
+            }
         }
     }
 }
@@ -190,6 +290,44 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const FillArgs &F,
     __syncwarp();
     const int ns = nslow;
     const int sp_n = A - 1;
+    if (MODE == 1 && !K1 && F.K >= kLaneSets) {
+        // K sets: one element at a time; lanes over spectators find the table
+        // entries, then lanes over sets sum them in spectator order
+        int2 *spec = reinterpret_cast<int2 *>(const_cast<int16_t *>(w_occ) + kMaxA);
+        for (int e = 0; e < ns; ++e) {
+            const uint32_t code = w_scode[e];
+            const int base = (code >> 31) ? nbase : 0;
+            const int a = base + (int)(code & 0xFF), c = base + (int)((code >> 8) & 0xFF);
+            const int sgn = (code >> 16) & 1;
+            int ia = 0;
+            for (int x = 0; x < A; ++x) ia += (w_occ[x] < a);
+            if (lane < sp_n) {
+                const int kspec = w_occ[lane + (lane >= ia ? 1 : 0)];
+                int64_t idx = 0;
+                int sg = 1;
+                const bool ok = tbme_at(B, a, kspec, c, kspec, idx, sg);
+                if (!ok && atomicOr(status, 1) == 0) {
+                    status[2] = a | (c << 16);
+                    status[3] = 2 | (kspec << 8);
+                }
+                spec[lane] = make_int2(ok ? (int)idx : -1, sg);
+            }
+            __syncwarp();
+            const int eo = w_spos[e];
+            for (int k = lane; k < F.K; k += 32) {
+                double v = 0.0;
+                for (int i = 0; i < sp_n; ++i) {
+                    const int2 q = spec[i];
+                    if (q.x >= 0) v += q.y * (double)__ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)q.x * F.tb_si);
+                }
+                R.val[(int64_t)eo * R.es + (int64_t)k * R.ks] = (float)(sgn ? -v : v);
+            }
+            if (lane == 0) R.col[eo] = w_scol[e];
+            __syncwarp();
+        }
+        nslow = 0;
+        return;
+    }
     int gsz = 1;
     while (gsz < sp_n) gsz <<= 1;
     const int per = 32 / gsz;
@@ -222,7 +360,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const FillArgs &F,
                 v = warp_sum(v, gsz);
                 if (act && i == 0) {
                     if (kk == 0) R.col[eo] = (int32_t)colj;
-                    R.val[(int64_t)kk * R.nnz + eo] = (float)(sgn ? -v : v);
+                    R.val[(int64_t)eo * R.es + (int64_t)kk * R.ks] = (float)(sgn ? -v : v);
                 }
             } else if (has && ok) {
                 const double f = 2.0 * Gr.psi[(int64_t)kk * B.dim + R.row] * Gr.psi[(int64_t)kk * B.dim + colj];
@@ -271,6 +409,8 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     const int64_t gw = (blockIdx.x * (int64_t)kThreads + tid) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
     const int Zpro = B.nZ[0], Zneu = B.nZ[1];
+    // K sets, element-major values: warp-cooperative value writes
+    const bool coop = MODE == 1 && !K1 && F.em && F.vec4 && ((F.K >> 2) > 32 ? (F.K >> 2) % 32 == 0 : 32 % (F.K >> 2) == 0);
 
     for (int64_t row = gw; row < B.dim; row += nw) {
         const int p = B.row_p[row];
@@ -281,13 +421,14 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         const int64_t cbp = rbp - nbp;
         RowOut R;
         R.row = row;
-        R.nnz = nnz;
+        R.es = (MODE == 1 && F.em) ? F.K : 1;
+        R.ks = (MODE == 1 && F.em) ? 1 : nnz;
         int rowlen = 0;
         if (MODE == 1) {
             const int64_t r0 = rowptr[row];
             rowlen = (int)(min(rowptr[row + 1], nnz) - r0);
             R.col = F.col + r0;
-            R.val = F.val + r0;
+            R.val = F.val + r0 * R.es;
         }
         int nslow = 0;
 
@@ -298,7 +439,39 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                                     : (int16_t)(nbase + B.occ[1][(int64_t)n * Zneu + (i - Zpro)]);
             __syncwarp();
             const uint8_t *pi = sptr<uint8_t>(sb, sm::pi), *pj = sptr<uint8_t>(sb, sm::pj);
-            for (int k = 0; k < (MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++k) {
+            const bool kset = MODE == 1 && !K1 && F.K >= kLaneSets && npairs <= kSlowCap;
+            if (kset) {
+                // K sets: the pairs' table entries in the (still empty) deferred
+                // queue arrays, then lanes over sets sum them in pair order
+                for (int l = lane; l < npairs; l += 32) {
+                    const int a = w_occ[pi[l]], c = w_occ[pj[l]];
+                    int64_t idx;
+                    int sg;
+                    const bool ok = tbme_at(B, a, c, a, c, idx, sg);
+                    if (!ok && atomicOr(status, 1) == 0) { status[2] = a | (c << 16); status[3] = 1; }
+                    w_scol[l] = ok ? (int32_t)idx : -1;
+                    w_scode[l] = sg < 0 ? 1u : 0u;
+                }
+                __syncwarp();
+                double one = 0.0;
+                for (int i = 0; i < A; ++i) {
+                    const int a = w_occ[i];
+                    one += F.esp ? F.esp[a] : F.hw * ((double)B.orbN[a] + 1.5);
+                }
+                for (int k = lane; k < F.K; k += 32) {
+                    double acc = 0.0;
+                    for (int l = 0; l < npairs; ++l) {
+                        const int32_t idx = w_scol[l];
+                        if (idx < 0) continue;
+                        const double v = (double)__ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)idx * F.tb_si);
+                        acc += w_scode[l] ? -v : v;
+                    }
+                    if (rowlen > 0) R.val[(int64_t)k * R.ks] = (float)(acc + one);
+                }
+                if (lane == 0 && rowlen > 0) R.col[0] = (int32_t)row;
+                __syncwarp();
+            }
+            for (int k = 0; k < (kset ? 0 : MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++k) {
                 double acc = 0.0;
                 for (int l = lane; l < npairs; l += 32) {
                     const int a = w_occ[pi[l]], c = w_occ[pj[l]];
@@ -324,7 +497,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     acc = warp_sum(acc, 32);
                     if (lane == 0 && rowlen > 0) {
                         if (k == 0) R.col[0] = (int32_t)row;
-                        R.val[(int64_t)k * nnz] = (float)acc;
+                        R.val[(int64_t)k * R.ks] = (float)acc;
                     }
                 }
             }
@@ -347,7 +520,12 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     const bool slow = in && tb < 0;
                     const unsigned smk = __ballot_sync(0xffffffffu, slow);
                     const int e = pos + __popc(bm & lt);
-                    if (in && !slow) put_single<MODE, K1>(B, F, Gr, R, e, cbp + y, tb >> 1, tb & 1);
+                    if (MODE == 1 && coop) {
+                        if (in && !slow) R.col[e] = (int32_t)(cbp + y);
+                        put_values_coop(F, R, in && !slow, tb >> 1, tb & 1, e);
+                    } else if (in && !slow) {
+                        put_single<MODE, K1>(B, F, Gr, R, e, cbp + y, tb >> 1, tb & 1);
+                    }
                     if (slow) {
                         const int q = nslow + __popc(smk & lt);
                         w_spos[q] = e;
@@ -398,10 +576,17 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 const int ins0 = self0 && !two0 ? self_rel - s0 : -1;     // where n sorts among the pn moves
                 const int ins1 = self1 && !two1 ? self_rel - s1 : -1;
                 // n itself: written (pp two-move) or deferred (one-proton move) by its candidate's lane
-                if (self0 && two0)
-                    put_single<MODE, K1>(B, F, Gr, R, ex0, (int64_t)r0.x + n, (int)((uint32_t)r0.z >> 1), r0.z & 1);
-                if (self1 && two1)
-                    put_single<MODE, K1>(B, F, Gr, R, ex1, (int64_t)r1.x + n, (int)((uint32_t)r1.z >> 1), r1.z & 1);
+                if (MODE == 1 && coop) {
+                    if (self0 && two0) R.col[ex0] = r0.x + n;
+                    if (self1 && two1) R.col[ex1] = r1.x + n;
+                    put_values_coop(F, R, self0 && two0, (int)((uint32_t)r0.z >> 1), r0.z & 1, ex0);
+                    put_values_coop(F, R, self1 && two1, (int)((uint32_t)r1.z >> 1), r1.z & 1, ex1);
+                } else {
+                    if (self0 && two0)
+                        put_single<MODE, K1>(B, F, Gr, R, ex0, (int64_t)r0.x + n, (int)((uint32_t)r0.z >> 1), r0.z & 1);
+                    if (self1 && two1)
+                        put_single<MODE, K1>(B, F, Gr, R, ex1, (int64_t)r1.x + n, (int)((uint32_t)r1.z >> 1), r1.z & 1);
+                }
                 const bool p0 = self0 && !two0, p1 = self1 && !two1;
                 const unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
                 if (nslow + __popc(m0) + __popc(m1) > kSlowCap)
@@ -452,16 +637,18 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                         if (ne1 && st1 >= w0 && st1 < w0 + 32) mk |= 1u << (st1 - w0);
                         mk = __reduce_or_sync(0xffffffffu, mk);
                         const int e = w0 + lane;
+                        int at = 0, idx = 0, sg = 0;
                         if (e < Tpn) {
                             const int j = before + __popc(mk & le) - 1;
                             const int4 sg4 = w_seg[j];
                             const int2 sx = w_ext[j];
-                            const int at = sg4.w + e + (e >= sx.y ? 1 : 0);
+                            at = sg4.w + e + (e >= sx.y ? 1 : 0);
                             const int2 ent = n1row[sx.x + e];
-                            int sg;
-                            const int idx = pn_index<WARPS>(sb, (uint32_t)sg4.y, (uint32_t)sg4.z, (uint32_t)ent.y, sg);
-                            put_single<MODE, K1>(B, F, Gr, R, at, (int64_t)(sg4.x + ent.x), idx, sg);
+                            idx = pn_index<WARPS>(sb, (uint32_t)sg4.y, (uint32_t)sg4.z, (uint32_t)ent.y, sg);
+                            if (MODE == 1 && coop) R.col[at] = sg4.x + ent.x;
+                            else put_single<MODE, K1>(B, F, Gr, R, at, (int64_t)(sg4.x + ent.x), idx, sg);
                         }
+                        if (MODE == 1 && coop) put_values_coop(F, R, e < Tpn, idx, sg, at);
                         before += __popc(mk);
                     }
                     __syncwarp();
@@ -561,9 +748,11 @@ int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st)
 }
 
 int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved,
-                const double *esp, int32_t *col, float *val, cudaStream_t st)
+                bool em, const double *esp, int32_t *col, float *val, cudaStream_t st)
 {
-    FillArgs F{K, hw, tbme, interleaved ? 1 : b.layout.total, interleaved ? (int64_t)K : 1, esp, col, val};
+    const int vec4 = interleaved && K % 4 == 0 && ((uintptr_t)tbme & 15) == 0 && (!em || ((uintptr_t)val & 15) == 0);
+    FillArgs F{K, hw, tbme, interleaved ? 1 : b.layout.total, interleaved ? (int64_t)K : 1, vec4, em && K > 1 ? 1 : 0,
+               esp, col, val};
     return launch_rows<1>(b, rowptr, nullptr, F, GradArgs{}, st);
 }
 

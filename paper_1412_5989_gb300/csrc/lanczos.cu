@@ -241,7 +241,7 @@ int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter)
 }
 
 int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val, int K, int nev,
-            int max_iter, double tol, double *evals, double *evec0, cudaStream_t st)
+            int max_iter, double tol, double *evals, double *evec0, cudaStream_t st, bool values_em)
 {
     const int64_t dim = b.dim;
     for (int k = 0; k < K * nev; ++k) evals[k] = NAN;
@@ -272,7 +272,7 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
               alloc((void **)&w, sizeof(double) * vstride) &&
               alloc((void **)&partial, sizeof(double) * (size_t)(m_max + 1) * K * kDotBlocks) &&
               alloc((void **)&hdev, sizeof(double) * (size_t)(m_max + 1) * K) && alloc((void **)&fdev, sizeof(double) * K);
-    if (ok && K > 1) ok = alloc((void **)&vem, sizeof(float) * (size_t)nnz * K);
+    if (ok && K > 1 && !values_em) ok = alloc((void **)&vem, sizeof(float) * (size_t)nnz * K);
     int rc = ok ? CIH_OK : fail(CIH_ERR_NOMEM, "lanczos: device memory");
     const int g = grid_for(vstride);
     const int gr = (int)std::min<int64_t>((dim + 7) / 8, 152 * 32);
@@ -301,11 +301,11 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
             cudaFuncSetAttribute(k_tsort<kTileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kTileLarge * (int)sizeof(int64_t));
             k_tsort<kTileLarge><<<152, 1024, kTileLarge * sizeof(int64_t), st>>>(dim, toff, tent, kTileSmall);
-            if (K > 1) {
+            if (K > 1 && !values_em) {
                 count_launches(1);
                 k_vals_em<<<grid_for(nnz * K), kThreads, 0, st>>>(K, nnz, val, vem);
             } else {
-                vem = const_cast<float *>(val);
+                vem = const_cast<float *>(val);                     // already element-major
             }
             e = cudaStreamSynchronize(st);                          // the host offsets go out of scope here
             if (e != cudaSuccess) rc = cuda_fail(e, "lanczos: transpose");

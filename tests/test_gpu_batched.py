@@ -1,8 +1,10 @@
 """GPU: K interaction sets sharing one structure (4+4 Nmax=4, 2M=0, K=64).
 
-- the set-major and the element-major (interleaved) fills agree bit for bit,
-  and with K independent single-set fills (the K loop only repeats the same
-  FP64 sums per set);
+- the set-major fill, the fill from interleaved tables and the batched fill
+  (element-major values) agree bit for bit; against K independent single-set
+  fills the structure is bit-identical and the values agree within 1e-6
+  (multi-term values are summed in term order per set, the single-set fill
+  sums them as a warp tree);
 - sampled rows of two sets agree with the oracle;
 - every launch shape the autotuner tries gives the same bits;
 - count + scan + fill captured in one CUDA graph and replayed agree with the
@@ -55,12 +57,25 @@ def test_interleaved_equals_set_major(cih, built):
     del col2, val2, til
 
 
+def test_batched_element_major(cih, built):
+    B, T, rowptr, nnz, col, val = built
+    til = cih.tbme_interleave(T)
+    c3, vem = B.fill_batched(rowptr, nnz, til, K)
+    B.check()
+    assert vem.shape == (nnz, K)
+    assert torch.equal(c3, col)
+    assert torch.equal(vem.t(), val)
+    del c3, vem, til
+
+
 @pytest.mark.parametrize("k", [0, 17, 63])
 def test_batched_equals_single(cih, built, k):
     B, T, rowptr, nnz, col, val = built
     c1, v1 = B.fill(rowptr, nnz, T[k].contiguous())
     assert torch.equal(c1, col)
-    assert torch.equal(v1[0], val[k])
+    a, b = v1[0].double(), val[k].double()
+    assert torch.all((a - b).abs() <= 1e-6 * (b.abs() + 1.0))
+    assert (a == b).double().mean() > 0.999
 
 
 def test_batched_sampled_rows_against_oracle(cih, built):
@@ -94,6 +109,8 @@ def test_launch_shapes_and_autotuner(cih, built):
     til = cih.tbme_interleave(T8)
     c4, v4, _ = B.autotune_fill(rowptr, nnz, til, K=8, interleaved=True)
     assert torch.equal(c4, ref_c) and torch.equal(v4, ref_v)
+    c5, v5, _ = B.autotune_fill(rowptr, nnz, til, K=8, batched=True)
+    assert torch.equal(c5, ref_c) and torch.equal(v5.t(), ref_v)
     B.set_launch(16, 0)
     with pytest.raises(cih.CihError):
         B.set_launch(12, 0)
@@ -130,7 +147,23 @@ def test_graph_capture_replay(cih, built):
         assert torch.equal(rp, rowptr)
         assert torch.equal(c[:nnz], col) and torch.equal(v[:, :nnz], val)
     B.check()
-    del g
+    del g, v
+    # the batched fill (interleaved tables, element-major values) in a graph
+    til = cih.tbme_interleave(T)
+    vem = torch.empty((nnz, K), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(s):
+        B.fill_batched(rp, nnz, til, K, stream=s, col=c, val=vem)
+    torch.cuda.synchronize()
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=s):
+        B.count_into(rp, stream=s)
+        B.fill_batched(rp, nnz, til, K, stream=s, col=c, val=vem)
+    vem.zero_()
+    g2.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(vem.t(), val)
+    B.check()
+    del g2, vem, til
 
 
 def test_batched_lanczos(cih, built):
@@ -138,6 +171,14 @@ def test_batched_lanczos(cih, built):
     ev, psi, conv = B.lanczos(rowptr, col, val, nev=5, max_iter=400, tol=1e-9)
     assert conv
     assert ev.shape == (K, 5) and np.all(np.diff(ev, axis=1) >= -1e-9)
+    # the same from the batched fill's element-major values, read in place
+    til = cih.tbme_interleave(T)
+    c3, vem = B.fill_batched(rowptr, nnz, til, K)
+    ev_em, psi_em, conv_em = B.lanczos(rowptr, c3, vem, nev=5, max_iter=400, tol=1e-9, element_major=True)
+    assert conv_em
+    np.testing.assert_array_equal(ev_em, ev)
+    assert torch.equal(psi_em, psi)
+    del c3, vem, til, psi_em
     # each set as a single-set run (same start vector; sums in another order)
     for k in (0, 31, 63):
         ev1, psi1, conv1 = B.lanczos(rowptr, col, val[k:k + 1], nev=5, max_iter=400, tol=1e-9)
