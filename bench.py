@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--workload", default="4p4n_nmax6", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched-fill and Lanczos side measurements")
+    ap.add_argument("--sets", type=int, default=1,
+                    help="K two-body tables (seeds seed..seed+K-1); K > 1 times the batched fill "
+                         "(interleaved tables, element-major values)")
     ap.add_argument("--cpu-rows", type=int, default=60000, help="rows in the oracle's timed sample")
     return ap.parse_args()
 
@@ -182,6 +186,61 @@ def whole_job_rate(world, steps, units_per_step, total_ms):
     return world * steps * units_per_step / (total_ms * 1e-3)
 
 
+def side_measurements(args, dev, st, flush, peak, cih, synth, sp, rowptr, col, val, nnz):
+    """Measurements beside the headline (not part of `value`): the batched fill
+    (4+4 Nmax=4, K=64 tables, element-major values) and Lanczos iterations on
+    the step's matrix.  CUDA events on the launching stream, L2 flushed."""
+    import torch
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    out = {}
+    K = 64
+    Bk = cih.Basis(4, 4, 4, 0)
+    T = torch.from_numpy(synth.tbme_tables(Bk.tbme_len, range(K))).to(dev)
+    til = cih.tbme_interleave(T)
+    rp4, n4 = Bk.count()
+    c4 = torch.empty(n4, dtype=torch.int32, device=dev)
+    v4 = torch.empty((n4, K), dtype=torch.float32, device=dev)
+    ms = timed(lambda: Bk.fill_batched(rp4, n4, til, K, col=c4, val=v4))
+    Bk.check()
+    gbs = n4 * (4 + 4 * K) / (ms * 1e-3) / 1e9
+    out["batched_fill"] = {"workload": "4p4n_nmax4_2M0_K64_seeds0-63", "layout": "interleaved tables, element-major values",
+                           "nnz_half": n4, "sets": K, "fill_ms": ms, "values_per_s": n4 * K / (ms * 1e-3),
+                           "achieved_gbs": gbs, "frac_of_hbm_peak": gbs / peak}
+    del c4, v4, T, til
+    Bk.close()
+    # Lanczos on the step's matrix: a fixed number of iterations (no convergence test passes)
+    Bl = cih.Basis(*sp)
+    Bl.count_into(rowptr)
+    Bl.fill(rowptr, nnz, torch.from_numpy(synth.tbme_table(Bl.tbme_len, 0)).to(dev), col=col, val=val)
+    iters = 40
+    t0 = cih.kernel_launches()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    Bl.lanczos(rowptr, col[:nnz], val[:, :nnz], nev=1, max_iter=iters, tol=1e-300, want_vectors=False)
+    b.record(st)
+    torch.cuda.synchronize()
+    out["lanczos"] = {"iterations": iters, "ms_total": a.elapsed_time(b), "ms_per_iteration": a.elapsed_time(b) / iters,
+                      "note": "includes the transposed-index build; FP64 vectors, two Gram-Schmidt passes per step",
+                      "kernel_launches": cih.kernel_launches() - t0}
+    Bl.close()
+    return out
+
+
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args, rank):
@@ -224,13 +283,19 @@ def run_ours(args, rank, world, local_rank):
     w = WORKLOADS[args.workload]
     sp = (w["Z"], w["N"], w["Nmax"], w["twoM"])
 
+    K = max(1, args.sets)
     B0 = cih.Basis(*sp)
     dim, tl = B0.dim, B0.tbme_len
     tbme_h = synth.tbme_table(tl, w["seed"])
     tbme = torch.from_numpy(tbme_h).to(dev)
     rowptr, nnz = B0.count()
     col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
-    val = torch.empty((1, max(nnz, 1)), dtype=torch.float32, device=dev)
+    if K == 1:
+        val = torch.empty((1, max(nnz, 1)), dtype=torch.float32, device=dev)
+    else:                                                    # K tables, interleaved once (not timed)
+        til = cih.tbme_interleave(torch.from_numpy(synth.tbme_tables(tl, range(w["seed"], w["seed"] + K))).to(dev))
+        val = torch.empty((max(nnz, 1), K), dtype=torch.float32, device=dev)
+    bytes_per_nnz = 4 + 4 * K                                # int32 column + K float32 values
     B0.close()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -240,7 +305,10 @@ def run_ours(args, rank, world, local_rank):
         ev[1].record(st)
         B.count_into(rowptr)                                 # count + scan
         ev[2].record(st)
-        B.fill(rowptr, nnz, tbme, col=col, val=val)          # fill: columns + values
+        if K == 1:
+            B.fill(rowptr, nnz, tbme, col=col, val=val)      # fill: columns + values
+        else:
+            B.fill_batched(rowptr, nnz, til, K, col=col, val=val)
         ev[3].record(st)
         return B
 
@@ -300,7 +368,7 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the public API with host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and K == 1:
         tb_pin = torch.from_numpy(tbme_h).pin_memory()
         col_h = torch.empty(nnz, dtype=torch.int32, pin_memory=True)
         val_h = torch.empty(nnz, dtype=torch.float32, pin_memory=True)
@@ -329,16 +397,18 @@ def run_ours(args, rank, world, local_rank):
         del col_h, val_h
 
     peak, peak_kind = measured_peak()
+    extra = {} if (args.no_extra or K > 1) else side_measurements(args, dev, st, flush, peak, cih, synth, sp, rowptr, col, val, nnz)
     fill_ms = statistics.median(t_fill)
-    achieved = nnz * BYTES_PER_NNZ / (fill_ms * 1e-3) / 1e9
+    achieved = nnz * bytes_per_nnz / (fill_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "kernel": "k_rows<4,1,K1> (fill)", "algorithmic_bytes_per_launch": nnz * BYTES_PER_NNZ,
-                "traffic": fill_traffic(kernel_source_sha())}
+                "kernel": "k_rows<W,1,K1> (fill)" if K == 1 else f"k_rows<W,1> (batched fill, K={K})",
+                "algorithmic_bytes_per_launch": nnz * bytes_per_nnz,
+                "traffic": fill_traffic(kernel_source_sha()) if (args.workload == "4p4n_nmax6" and K == 1) else None}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and K == 1:
         r, n, dt, threads, rows = oracle_rate(w, args.cpu_rows)
         cpu = {"value": r, "unit": "nnz/s", "cores": threads, "kind": "oracle",
                "sample": f"{rows} random rows of {args.workload} ({n} nonzeros, {dt:.1f} s): count + fill by "
@@ -350,7 +420,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(w), "dim": dim, "nnz_half": nnz, "tbme_entries": tl,
-                       "tbme_sets": 1, "l2": "flushed between steps (256 MiB write)",
+                       "tbme_sets": K, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "stages_ms": {"basis": statistics.median(t_basis), "count_scan": statistics.median(t_count),
                           "fill": fill_ms, "adjoint": statistics.median(tg)},
@@ -359,6 +429,7 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
+            **extra,
             "clocks": clocks,
         }), flush=True)
 

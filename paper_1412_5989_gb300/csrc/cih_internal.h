@@ -42,6 +42,7 @@ struct DevBasis {
     const int32_t *pid;        // ntot x ntot pair id (see pair_code), -1 = none
     const int32_t *gsize;      // per global group: pairs in the group
     const int64_t *goff;       // per global group: table offset of its triangle
+    int32_t ngroups;           // global groups of the table layout
     int32_t n_p;
     int32_t ntot;
     int64_t dim;

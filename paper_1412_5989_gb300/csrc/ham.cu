@@ -57,7 +57,11 @@ constexpr double kFixScale = 72057594037927936.0;   // 2^56
 
 // Table index of V(ab, cd) for combined orbitals in any order; false if the
 // pairs are not one table entry (a bug in the walk: flagged by the caller).
-__device__ __forceinline__ bool tbme_at(const DevBasis &B, int a, int b, int c, int d, int64_t &idx, int &sign)
+// The group sizes and offsets come from shared memory (lg: size and offset
+// per group, int2) when the layout has at most kLayoutCap groups.
+constexpr int kLayoutCap = 512;
+__device__ __forceinline__ bool tbme_at(const DevBasis &B, const int2 *lg, int a, int b, int c, int d, int64_t &idx,
+                                        int &sign)
 {
     if ((unsigned)a >= (unsigned)B.ntot || (unsigned)b >= (unsigned)B.ntot ||
         (unsigned)c >= (unsigned)B.ntot || (unsigned)d >= (unsigned)B.ntot)
@@ -67,10 +71,18 @@ __device__ __forceinline__ bool tbme_at(const DevBasis &B, int a, int b, int c, 
     int g = (e1 >> 16) & 0xFFF;
     if (g != ((e2 >> 16) & 0xFFF)) return false;
     sign = (((e1 ^ e2) >> 30) & 1) ? -1 : 1;
-    int64_t u = e1 & 0xFFFF, v = e2 & 0xFFFF;
-    if (u > v) { int64_t t = u; u = v; v = t; }
-    int64_t n = B.gsize[g];
-    idx = B.goff[g] + u * n - u * (u - 1) / 2 + (v - u);
+    int u = e1 & 0xFFFF, v = e2 & 0xFFFF;
+    if (u > v) { const int t = u; u = v; v = t; }
+    int64_t n, off;
+    if (B.ngroups <= kLayoutCap) {
+        const int2 q = lg[g];
+        n = q.x;
+        off = q.y;
+    } else {
+        n = B.gsize[g];
+        off = B.goff[g];
+    }
+    idx = off + (int64_t)u * n - (int64_t)u * (u - 1) / 2 + (v - u);
     return true;
 }
 
@@ -104,7 +116,8 @@ constexpr int gsize = 0;                                   // int32[kGroupCap]
 constexpr int goff = gsize + kGroupCap * 4;                // int32[kGroupCap]
 constexpr int pi = goff + kGroupCap * 4;                   // uint8[kPairCap]
 constexpr int pj = pi + kPairCap;                          // uint8[kPairCap]
-constexpr int warp0 = (pj + kPairCap + 15) / 16 * 16;
+constexpr int lg = (pj + kPairCap + 15) / 16 * 16;         // int2[kLayoutCap]: table group size, offset
+constexpr int warp0 = lg + kLayoutCap * 8;
 // per warp
 constexpr int w_seg = 0;                                   // int4[64]: colbase, uv, mv, row start
 constexpr int w_ext = w_seg + 64 * 16;                     // int2[64]: list start, insertion point
@@ -281,9 +294,10 @@ __device__ __forceinline__ void put_values_coop(const FillArgs &F, const RowOut 
 // The queue holds row-relative positions, columns and packed moves
 // (bra-only a, ket-only c, sign, neutron flag in bit 31).
 template <int MODE, bool K1>
-__device__ __forceinline__ void flush_slow(const DevBasis &B, const FillArgs &F, const GradArgs &Gr, int *status,
-                                           const int16_t *w_occ, const int32_t *w_spos, const int32_t *w_scol,
-                                           const uint32_t *w_scode, int &nslow, const RowOut &R)
+__device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, const FillArgs &F, const GradArgs &Gr,
+                                           int *status, const int16_t *w_occ, const int32_t *w_spos,
+                                           const int32_t *w_scol, const uint32_t *w_scode, int &nslow,
+                                           const RowOut &R)
 {
     const int lane = threadIdx.x & 31;
     const int A = B.A, nbase = B.sp[1].orb_base;
@@ -305,7 +319,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const FillArgs &F,
                 const int kspec = w_occ[lane + (lane >= ia ? 1 : 0)];
                 int64_t idx = 0;
                 int sg = 1;
-                const bool ok = tbme_at(B, a, kspec, c, kspec, idx, sg);
+                const bool ok = tbme_at(B, lg, a, kspec, c, kspec, idx, sg);
                 if (!ok && atomicOr(status, 1) == 0) {
                     status[2] = a | (c << 16);
                     status[3] = 2 | (kspec << 8);
@@ -348,7 +362,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const FillArgs &F,
         int64_t idx = 0;
         int sg = 1;
         bool ok = true;
-        if (has) ok = tbme_at(B, a, kspec, c, kspec, idx, sg);
+        if (has) ok = tbme_at(B, lg, a, kspec, c, kspec, idx, sg);
         if (!ok && atomicOr(status, 1) == 0) {
             status[2] = a | (c << 16);
             status[3] = 2 | (kspec << 8);
@@ -390,6 +404,10 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         int32_t *gs = sptr<int32_t>(sb, sm::gsize), *go = sptr<int32_t>(sb, sm::goff);
         for (int i = tid; i < nS; i += kThreads) S[i] = B.pn_S[i];
         for (int i = tid; i < G; i += kThreads) { gs[i] = B.pn_gsize[i]; go[i] = B.pn_goff[i]; }
+        if (B.ngroups <= kLayoutCap) {
+            int2 *lgw = sptr<int2>(sb, sm::lg);
+            for (int g = tid; g < B.ngroups; g += kThreads) lgw[g] = make_int2(B.gsize[g], (int)B.goff[g]);
+        }
         uint8_t *pi = sptr<uint8_t>(sb, sm::pi), *pj = sptr<uint8_t>(sb, sm::pj);
         for (int l = tid; l < npairs; l += kThreads) {     // pair l -> (i, j), i < j
             int i = 0, r = l;
@@ -400,6 +418,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         __syncthreads();
     }
     const int64_t nnz = MODE == 1 ? rowptr[B.dim] : 0;
+    const int2 *lg = sptr<int2>(sb, sm::lg);
     unsigned char *wb = sb + sm::warp0 + wid * sm::w_size;
     int4 *w_seg = sptr<int4>(wb, sm::w_seg);
     int2 *w_ext = sptr<int2>(wb, sm::w_ext);
@@ -447,7 +466,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     const int a = w_occ[pi[l]], c = w_occ[pj[l]];
                     int64_t idx;
                     int sg;
-                    const bool ok = tbme_at(B, a, c, a, c, idx, sg);
+                    const bool ok = tbme_at(B, lg, a, c, a, c, idx, sg);
                     if (!ok && atomicOr(status, 1) == 0) { status[2] = a | (c << 16); status[3] = 1; }
                     w_scol[l] = ok ? (int32_t)idx : -1;
                     w_scode[l] = sg < 0 ? 1u : 0u;
@@ -477,7 +496,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     const int a = w_occ[pi[l]], c = w_occ[pj[l]];
                     int64_t idx;
                     int sg;
-                    if (!tbme_at(B, a, c, a, c, idx, sg)) {
+                    if (!tbme_at(B, lg, a, c, a, c, idx, sg)) {
                         if (atomicOr(status, 1) == 0) { status[2] = a | (c << 16); status[3] = 1; }
                         continue;
                     }
@@ -510,13 +529,14 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
             for (int64_t t0 = a0; t0 < a1; t0 += 32) {
                 const int64_t t = t0 + lane;
                 const int y = t < a1 ? SN.fw[t] : INT32_MAX;
+                const int32_t tbl = (MODE != 0 && t < a1) ? B.fw_tb[1][t] : 0;    // loaded beside y
                 const bool in = y < nend;
                 const unsigned bm = __ballot_sync(0xffffffffu, in);
                 if (MODE != 0) {
                     if (MODE == 1 && pos + __popc(bm) > rowlen) { atomicOr(status, 2); break; }
                     if (nslow > kSlowCap - 32)
-                        flush_slow<MODE, K1>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
-                    const int32_t tb = in ? B.fw_tb[1][t] : 0;
+                        flush_slow<MODE, K1>(B, lg, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
+                    const int32_t tb = in ? tbl : 0;
                     const bool slow = in && tb < 0;
                     const unsigned smk = __ballot_sync(0xffffffffu, slow);
                     const int e = pos + __popc(bm & lt);
@@ -590,7 +610,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 const bool p0 = self0 && !two0, p1 = self1 && !two1;
                 const unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
                 if (nslow + __popc(m0) + __popc(m1) > kSlowCap)
-                    flush_slow<MODE, K1>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
+                    flush_slow<MODE, K1>(B, lg, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
                 if (p0) {
                     const int q = nslow + __popc(m0 & lt);
                     const uint32_t mv = (uint32_t)r0.w;
@@ -656,7 +676,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
             }
             pos += T;
         }
-        if (MODE != 0 && nslow > 0) flush_slow<MODE, K1>(B, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
+        if (MODE != 0 && nslow > 0) flush_slow<MODE, K1>(B, lg, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
         if (MODE == 0 && lane == 0) counts[row] = pos;
         __syncwarp();
     }

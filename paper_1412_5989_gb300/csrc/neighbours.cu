@@ -836,6 +836,7 @@ int basis_tables_upload(cih_basis &b, cudaStream_t st)
     b.dev.pid = d_pid;
     b.dev.gsize = d_gsize;
     b.dev.goff = d_goff;
+    b.dev.ngroups = (int32_t)b.layout.gsize.size();
     b.dev.n_p = (int32_t)b.s[0].n_sd;
     b.dev.ntot = ntot;
     b.dev.dim = b.dim;
