@@ -35,15 +35,19 @@ __global__ void k_tcount(int64_t dim, const int64_t *rowptr, const int32_t *col,
             if (col[k] != i) atomicAdd(&tcnt[col[k]], 1);
 }
 
+// entry of stored nonzero k = (i, j), i < j, in column j's list: (i << 32) |
+// low, low = the value's bits when one set (the mirror pass then reads no
+// other array), else k
 __global__ void k_tfill(int64_t dim, const int64_t *rowptr, const int32_t *col, const int64_t *toff, int32_t *tcur,
-                        int64_t *tent)
+                        const float *val1, int64_t *tent)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x)
         for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
             const int32_t j = col[k];
             if (j == i) continue;
             const int64_t at = toff[j] + atomicAdd(&tcur[j], 1);
-            tent[at] = (i << 32) | (uint32_t)k;              // sorts by row first
+            const uint32_t low = val1 ? __float_as_uint(val1[k]) : (uint32_t)k;
+            tent[at] = (i << 32) | low;                      // sorts by row first
         }
 }
 
@@ -80,6 +84,16 @@ __global__ void k_tsort(int64_t dim, const int64_t *toff, int64_t *tent, int lo)
 }
 constexpr int kTileSmall = 2048, kTileLarge = 16384;   // 16 KB and 128 KB of shared memory
 
+// values of the transposed entries, element-major: vT[t * K + s] = vem[k(t) * K + s]
+__global__ void k_vT(int64_t nt, int K, const int64_t *tent, const float *vem, float *vT)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nt * K; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = q / K;
+        const int s = (int)(q - t * K);
+        vT[q] = vem[(int64_t)(uint32_t)tent[t] * K + s];
+    }
+}
+
 // element-major values: vem[k * K + s] = val[s * nnz + k]
 __global__ void k_vals_em(int K, int64_t nnz, const float *val, float *vem)
 {
@@ -95,7 +109,7 @@ __global__ void k_vals_em(int K, int64_t nnz, const float *val, float *vem)
 // then reduce across the groups.
 template <int KS>
 __global__ void k_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t *col, const int64_t *toff,
-                       const int64_t *tent, const float *vem, const double *x, double *y)
+                       const int64_t *tent, const float *vem, const float *vT, const double *x, double *y)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -106,10 +120,8 @@ __global__ void k_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t 
             for (int s = lane; s < K; s += 32) {
                 double acc = 0.0;
                 for (int64_t k = a0; k < a1; ++k) acc += (double)vem[k * K + s] * x[(int64_t)col[k] * K + s];
-                for (int64_t t = b0; t < b1; ++t) {
-                    const int64_t e = tent[t];
-                    acc += (double)vem[(int64_t)(uint32_t)e * K + s] * x[(e >> 32) * K + s];
-                }
+                for (int64_t t = b0; t < b1; ++t)
+                    acc += (double)vT[t * K + s] * x[(tent[t] >> 32) * K + s];
                 y[i * K + s] = acc;
             }
         } else {
@@ -119,7 +131,8 @@ __global__ void k_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t 
                 for (int64_t k = a0 + g; k < a1; k += G) acc += (double)vem[k * K + s] * x[(int64_t)col[k] * K + s];
                 for (int64_t t = b0 + g; t < b1; t += G) {
                     const int64_t e = tent[t];
-                    acc += (double)vem[(int64_t)(uint32_t)e * K + s] * x[(e >> 32) * K + s];
+                    const float v = KS == 1 ? __uint_as_float((uint32_t)e) : vT[t * K + s];
+                    acc += (double)v * x[(e >> 32) * K + s];
                 }
             }
             for (int d = 16; d >= KS; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
@@ -236,7 +249,7 @@ int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter)
     int64_t bytes = 4 * (dim + 1) + 8 * (dim + 1) + 8 * nt;          // transposed index
     bytes += 8 * (m + 1) * dim * K + 8 * dim * K;                   // Lanczos vectors, w
     bytes += 8 * (m + 1) * K * kDotBlocks + 8 * (m + 1) * K + 8 * K; // dot partials, h, scale
-    if (K > 1) bytes += 4 * nnz * K;                                // element-major values
+    if (K > 1) bytes += 4 * nnz * K + 4 * nt * K;                   // element-major values, mirror values
     return bytes + 8 * 256;                                         // allocation granules
 }
 
@@ -263,7 +276,7 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
     };
     int32_t *tcnt = nullptr;
     int64_t *toff = nullptr, *tent = nullptr;
-    float *vem = nullptr;
+    float *vem = nullptr, *vT = nullptr;
     double *V = nullptr, *w = nullptr, *partial = nullptr, *hdev = nullptr, *fdev = nullptr;
     const int64_t nt = std::max<int64_t>(nnz - dim, 1);             // strictly upper entries
     bool ok = alloc((void **)&tcnt, sizeof(int32_t) * (dim + 1)) && alloc((void **)&toff, sizeof(int64_t) * (dim + 1)) &&
@@ -273,6 +286,7 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
               alloc((void **)&partial, sizeof(double) * (size_t)(m_max + 1) * K * kDotBlocks) &&
               alloc((void **)&hdev, sizeof(double) * (size_t)(m_max + 1) * K) && alloc((void **)&fdev, sizeof(double) * K);
     if (ok && K > 1 && !values_em) ok = alloc((void **)&vem, sizeof(float) * (size_t)nnz * K);
+    if (ok && K > 1) ok = alloc((void **)&vT, sizeof(float) * (size_t)nt * K);
     int rc = ok ? CIH_OK : fail(CIH_ERR_NOMEM, "lanczos: device memory");
     const int g = grid_for(vstride);
     const int gr = (int)std::min<int64_t>((dim + 7) / 8, 152 * 32);
@@ -292,7 +306,7 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
             cudaMemcpyAsync(toff, ho.data(), sizeof(int64_t) * (dim + 1), cudaMemcpyHostToDevice, st);
             cudaMemsetAsync(tcnt, 0, sizeof(int32_t) * (dim + 1), st);
             count_launches(1);
-            k_tfill<<<grid_for(dim), kThreads, 0, st>>>(dim, rowptr, col, toff, tcnt, tent);
+            k_tfill<<<grid_for(dim), kThreads, 0, st>>>(dim, rowptr, col, toff, tcnt, K == 1 ? val : nullptr, tent);
             // columns up to 2048 entries, then the longer ones (up to 16384) one per SM;
             // longer columns keep the fill order, which may vary from run to run
             const int gs = (int)std::min<int64_t>(dim, 65535);
@@ -307,6 +321,10 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
             } else {
                 vem = const_cast<float *>(val);                     // already element-major
             }
+            if (K > 1 && nnz > dim) {                               // mirror values in column order
+                count_launches(1);
+                k_vT<<<grid_for((nnz - dim) * K), kThreads, 0, st>>>(nnz - dim, K, tent, vem, vT);
+            }
             e = cudaStreamSynchronize(st);                          // the host offsets go out of scope here
             if (e != cudaSuccess) rc = cuda_fail(e, "lanczos: transpose");
         }
@@ -314,12 +332,12 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
 
     auto spmv = [&](const double *x, double *y) {
         count_launches(1);
-        if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, x, y);
-        else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, x, y);
-        else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, x, y);
-        else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, x, y);
-        else if (K <= 8) k_spmv<8><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, x, y);
-        else k_spmv<16><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, x, y);
+        if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
+        else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
+        else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
+        else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
+        else if (K <= 8) k_spmv<8><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
+        else k_spmv<16><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
     };
     // h[r][s] = V[r] . w for r < nvec: into hdev (device) and hh (host)
     std::vector<double> hh((size_t)(m_max + 1) * K);
