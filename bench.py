@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched-fill and Lanczos side measurements")
+    ap.add_argument("--extra", choices=["all", "batched", "lanczos"], default="all",
+                    help="which side measurements to run (default all)")
     ap.add_argument("--sets", type=int, default=1,
                     help="K two-body tables (seeds seed..seed+K-1); K > 1 times the batched fill "
                          "(interleaved tables, element-major values)")
@@ -207,6 +209,17 @@ def side_measurements(args, dev, st, flush, peak, cih, synth, sp, rowptr, col, v
         return statistics.median(ts)
 
     out = {}
+    if args.extra in ("all", "batched"):
+        out.update(batched_fill_measurement(dev, st, peak, cih, synth, timed))
+    if args.extra in ("all", "lanczos"):
+        out.update(lanczos_measurement(args, dev, st, cih, synth, sp, rowptr, col, val, nnz))
+    return out
+
+
+def batched_fill_measurement(dev, st, peak, cih, synth, timed):
+    """4+4 Nmax=4, K = 64 tables: the batched fill and Lanczos on the 64 matrices."""
+    import torch
+    out = {}
     K = 64
     Bk = cih.Basis(4, 4, 4, 0)
     T = torch.from_numpy(synth.tbme_tables(Bk.tbme_len, range(K))).to(dev)
@@ -233,7 +246,13 @@ def side_measurements(args, dev, st, flush, peak, cih, synth, sp, rowptr, col, v
     out["batched_fill"]["lanczos_64_sets"] = {"setup_ms": t1, "ms_per_iteration": (t11 - t1) / 10}
     del c4, v4, T, til
     Bk.close()
-    # Lanczos on the step's matrix: a fixed number of iterations (no convergence test passes)
+    return out
+
+
+def lanczos_measurement(args, dev, st, cih, synth, sp, rowptr, col, val, nnz):
+    """Lanczos on the step's matrix: a fixed number of iterations (no convergence test passes)."""
+    import torch
+    out = {}
     Bl = cih.Basis(*sp)
     Bl.count_into(rowptr)
     Bl.fill(rowptr, nnz, torch.from_numpy(synth.tbme_table(Bl.tbme_len, 0)).to(dev), col=col, val=val)

@@ -104,35 +104,97 @@ __global__ void k_vals_em(int K, int64_t nnz, const float *val, float *vem)
     }
 }
 
-// ---- y = H x for K sets.  One warp per row.  K >= 32: lanes over sets;
-// K < 32 (KS = next power of two): 32/KS lane groups split the nonzeros,
-// then reduce across the groups.
+// ---- y = H x for K sets.  One warp per row, row part then mirror part.
+// K >= 32: lanes over sets, two sets per lane per pass, nonzeros four at a
+// time; K < 32 (KS = next power of two): 32/KS lane groups split the
+// nonzeros, four per group at a time, then reduce across the groups.  The
+// four independent loads keep more of each row's gathers in flight.  The
+// summation order depends only on the structure.
 template <int KS>
 __global__ void k_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t *col, const int64_t *toff,
                        const int64_t *tent, const float *vem, const float *vT, const double *x, double *y)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < dim; i += nw) {
+    // each block walks one contiguous run of rows, so that rows of the same
+    // proton sub-determinant (which gather the same x blocks) share its L1
+    const int64_t per = (dim + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = blockIdx.x * per, r1 = min(dim, r0 + per);
+    const int wpb = blockDim.x >> 5;
+    for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += wpb) {
         const int64_t a0 = rowptr[i], a1 = rowptr[i + 1], b0 = toff[i], b1 = toff[i + 1];
         if (KS >= 32) {
-            for (int s = lane; s < K; s += 32) {
-                double acc = 0.0;
-                for (int64_t k = a0; k < a1; ++k) acc += (double)vem[k * K + s] * x[(int64_t)col[k] * K + s];
-                for (int64_t t = b0; t < b1; ++t)
-                    acc += (double)vT[t * K + s] * x[(tent[t] >> 32) * K + s];
-                y[i * K + s] = acc;
+            for (int s0 = 0; s0 < K; s0 += 64) {
+                const int sa = s0 + lane, sb = s0 + 32 + lane;
+                const bool ha = sa < K, hb = sb < K;
+                double acc_a = 0.0, acc_b = 0.0;
+                int64_t k = a0;
+                for (; k + 3 < a1; k += 4) {
+                    int64_t c[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) c[u] = (int64_t)col[k + u] * K;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (ha) acc_a += (double)vem[(k + u) * K + sa] * __ldg(x + c[u] + sa);
+                        if (hb) acc_b += (double)vem[(k + u) * K + sb] * __ldg(x + c[u] + sb);
+                    }
+                }
+                for (; k < a1; ++k) {
+                    const int64_t c = (int64_t)col[k] * K;
+                    if (ha) acc_a += (double)vem[k * K + sa] * __ldg(x + c + sa);
+                    if (hb) acc_b += (double)vem[k * K + sb] * __ldg(x + c + sb);
+                }
+                int64_t t = b0;
+                for (; t + 3 < b1; t += 4) {
+                    int64_t r[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) r[u] = (tent[t + u] >> 32) * K;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (ha) acc_a += (double)vT[(t + u) * K + sa] * __ldg(x + r[u] + sa);
+                        if (hb) acc_b += (double)vT[(t + u) * K + sb] * __ldg(x + r[u] + sb);
+                    }
+                }
+                for (; t < b1; ++t) {
+                    const int64_t r = (tent[t] >> 32) * K;
+                    if (ha) acc_a += (double)vT[t * K + sa] * __ldg(x + r + sa);
+                    if (hb) acc_b += (double)vT[t * K + sb] * __ldg(x + r + sb);
+                }
+                if (ha) y[i * K + sa] = acc_a;
+                if (hb) y[i * K + sb] = acc_b;
             }
         } else {
-            const int G = 32 / KS, g = lane / KS, s = lane % KS;
+            constexpr int G = 32 / KS;
+            const int g = lane / KS, s = lane % KS;
             double acc = 0.0;
             if (s < K) {
-                for (int64_t k = a0 + g; k < a1; k += G) acc += (double)vem[k * K + s] * x[(int64_t)col[k] * K + s];
-                for (int64_t t = b0 + g; t < b1; t += G) {
+                int64_t k = a0 + g;
+                for (; k + 3 * G < a1; k += 4 * G) {
+                    int64_t c[4];
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        c[u] = col[k + u * G];
+                        v[u] = vem[(k + u * G) * K + s];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc += (double)v[u] * __ldg(x + c[u] * K + s);
+                }
+                for (; k < a1; k += G) acc += (double)vem[k * K + s] * __ldg(x + (int64_t)col[k] * K + s);
+                int64_t t = b0 + g;
+                for (; t + 3 * G < b1; t += 4 * G) {
+                    int64_t e[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) e[u] = tent[t + u * G];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float v = KS == 1 ? __uint_as_float((uint32_t)e[u]) : vT[(t + u * G) * K + s];
+                        acc += (double)v * __ldg(x + (e[u] >> 32) * K + s);
+                    }
+                }
+                for (; t < b1; t += G) {
                     const int64_t e = tent[t];
                     const float v = KS == 1 ? __uint_as_float((uint32_t)e) : vT[t * K + s];
-                    acc += (double)v * x[(e >> 32) * K + s];
+                    acc += (double)v * __ldg(x + (e >> 32) * K + s);
                 }
             }
             for (int d = 16; d >= KS; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
