@@ -74,8 +74,15 @@ struct Enumerator {
         for (int c = 0; c < s.Z && c < (int)m.size(); ++c) Mabs += m[c];
         nN = s.Nsub_max + 1;
     }
-    int64_t nkeys() const { return (int64_t)(2 * Mabs + 1) * 2 * nN; }
-    int64_t key(int N, int M) const { return ((int64_t)(M + Mabs) * 2 + (N & 1)) * nN + N; }
+    // bucket key in (2M, N mod 2, N) order.  2M has the parity of Z (every 2m is
+    // odd), as has Mabs, so (2M + Mabs) / 2 numbers the possible 2M values;
+    // N maps to its rank among the even values, then the odd ones.
+    int64_t nkeys() const { return (int64_t)(Mabs + 1) * nN; }
+    int64_t key(int N, int M) const
+    {
+        const int r = (N & 1) ? (nN + 1) / 2 + (N >> 1) : (N >> 1);
+        return (int64_t)((M + Mabs) >> 1) * nN + r;
+    }
 
     // c more orbitals below `lim` with at most `budget` quanta; F(w, N, M) at each leaf
     template <class Fn>

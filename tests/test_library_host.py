@@ -112,3 +112,40 @@ def test_tridiagonal_eigensolver(cih):
     np.testing.assert_allclose(w, 2 - 2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)), atol=1e-13)
     w, Z = cih.tridiag_eigen(np.array([3.0, 1.0, 2.0]), np.zeros(2))
     assert w.tolist() == [1.0, 2.0, 3.0]
+
+
+def test_entry_points_reject_bad_arguments_without_a_gpu(cih):
+    """Argument checks of the device entry points run before any device work:
+    a host-only handle, NULL arrays, K, nev or budget out of range."""
+    import ctypes as C
+    lib = cih.lib
+    B = cih.Basis(3, 3, 2, 0, host_only=True)
+    h = B._h
+    assert lib.cih_tbme_interleave(0, 10, None, None, None) == -1
+    assert lib.cih_tbme_interleave(4, -1, None, None, None) == -1
+    assert lib.cih_set_launch(h, 12, 0) == -1
+    assert lib.cih_set_launch(h, 16, 33) == -1
+    assert lib.cih_set_launch(None, 16, 0) == -1
+    assert lib.cih_set_launch(h, 8, 2) == 0 and lib.cih_set_launch(h, 16, 0) == 0
+    rc = C.c_int32()
+    # device calls refuse a host-only handle
+    assert lib.cih_ham_count(h, C.c_void_p(16), None, None) == -1
+    assert lib.cih_ham_fill(h, C.c_void_p(16), 1, 20.0, C.c_void_p(16), None, C.c_void_p(16), C.c_void_p(16), None) == -1
+    assert lib.cih_ham_fill_batched(h, C.c_void_p(16), 4, 20.0, C.c_void_p(16), None, C.c_void_p(16),
+                                    C.c_void_p(16), None) == -1
+    ev = (C.c_double * 4)()
+    assert lib.cih_lanczos_lowest_em(h, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), 1, 1, 10, 1e-8, ev,
+                                     None, None) == -1
+    w, c, ms = C.c_int32(), C.c_int32(), C.c_float()
+    assert lib.cih_autotune_fill(h, C.c_void_p(16), 1, 20.0, C.c_void_p(16), 0, None, C.c_void_p(16),
+                                 C.c_void_p(16), None, C.byref(w), C.byref(c), C.byref(ms)) == -1
+    # batch: empty batch is a no-op, negative count, bad nev / budget, host-only instance
+    assert lib.cih_batch_solve(None, 0, 20.0, 5, 100, 1e-8, 0, None) == 0
+    assert lib.cih_batch_solve(None, -1, 20.0, 5, 100, 1e-8, 0, None) == -1
+    inst = (cih.Instance * 1)()
+    inst[0] = cih.Instance(h, 1, None, None, ev, None, 0, 0, -1, 0)
+    assert lib.cih_batch_solve(inst, 1, 20.0, 0, 100, 1e-8, 0, None) == -1
+    assert lib.cih_batch_solve(inst, 1, 20.0, 1, 100, 1e-8, -5, None) == -1
+    assert lib.cih_batch_solve(inst, 1, 20.0, 1, 100, 1e-8, 0, None) == -1     # host-only basis
+    assert lib.cih_batch_solve(inst, 300, 20.0, 1, 100, 1e-8, 0, None) == -5   # too many instances
+    B.close()
