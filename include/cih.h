@@ -160,6 +160,27 @@ int cih_ham_fill_batched(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, do
                          const float *tbme_il_dev, const double *e_sp_dev, int32_t *col_dev, float *val_em_dev,
                          void *stream);
 
+/* End to end with host memory (Sec. 2 and 4.1 as cih_ham_count + cih_ham_fill,
+ * with the host copies inside the call): the K two-body tables are copied
+ * host -> device, the count pass and scan run, the row pointers come back
+ * (one synchronisation, which gives nnz), then the fill runs in 8 row chunks
+ * of about equal nonzero counts while a second stream copies each finished
+ * chunk's columns and values device -> host.
+ *   tbme_host: K x tbme_len float (set-major); e_sp_host: NULL or
+ *   n_orb_p + n_orb_n double; rowptr_host: dim + 1 int64; col_host:
+ *   capacity int32; val_host: K x capacity float, the values of set k at
+ *   val_host[k * capacity + e]; *nnz_out (may be NULL): stored nonzeros.
+ * Host arrays should be page-locked (cudaHostAlloc, cudaHostRegister, a
+ * pinned torch tensor): then the copies run at link speed and overlap the
+ * fill; pageable memory works, but each copy then waits for its data.
+ * Device scratch (tables, row pointers, columns, K x values) is
+ * library-allocated for the call.  Synchronises `stream`.
+ * Errors: CIH_ERR_ARG; CIH_ERR_CAPACITY when nnz > capacity (rowptr_host and
+ * *nnz_out are written, nothing else); CIH_ERR_NOMEM; CIH_ERR_CUDA. */
+int cih_ham_build_host(cih_basis_h h, int32_t K, double hbar_omega, const float *tbme_host, const double *e_sp_host,
+                       int64_t *rowptr_host, int32_t *col_host, float *val_host, int64_t capacity, int64_t *nnz_out,
+                       void *stream);
+
 /* tbme_il_dev[t * K + k] = tbme_dev[k * tbme_len + t] (device arrays, caller-
  * owned, stream-ordered).  Errors: CIH_ERR_ARG, CIH_ERR_CUDA. */
 int cih_tbme_interleave(int32_t K, int64_t tbme_len, const float *tbme_dev, float *tbme_il_dev, void *stream);

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcih.so")
-SOURCES = ["basis.cpp", "capi.cpp", "tridiag.cpp", "neighbours.cu", "scan.cu", "ham.cu", "lanczos.cu", "batch.cpp"]
+SOURCES = ["basis.cpp", "capi.cpp", "tridiag.cpp", "neighbours.cu", "scan.cu", "ham.cu", "lanczos.cu", "batch.cpp", "host_io.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -48,6 +48,7 @@ _SIGS = {
     "cih_ham_fill_interleaved": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
     "cih_ham_fill_batched": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
     "cih_tbme_interleave": [C.c_int32, C.c_int64, _P, _P, _P],
+    "cih_ham_build_host": [_P, C.c_int32, C.c_double, _P, _P, _P, _P, _P, C.c_int64, _i64p, _P],
     "cih_set_launch": [_P, C.c_int32, C.c_int32],
     "cih_autotune_fill": [_P, _P, C.c_int32, C.c_double, _P, C.c_int32, _P, _P, _P, _P,
                           _i32p, _i32p, C.POINTER(C.c_float)],
@@ -270,6 +271,33 @@ class Basis:
         _ok(lib.cih_ham_fill_batched(self._h, _ptr(rowptr), K, float(hbar_omega), _ptr(tbme_il.contiguous()),
                                      _ptr(e_sp), _ptr(col), _ptr(val), _stream(stream)), "ham_fill_batched")
         return col[:nnz], val[:nnz]
+
+    def build_to_host(self, tbme, rowptr, col, val, hbar_omega: float = 20.0, e_sp=None, stream=None):
+        """End to end with host memory (cih_ham_build_host): tbme (K, tbme_len)
+        float32 host array or CPU tensor; rowptr (dim + 1,) int64, col
+        (capacity,) int32 and val (K, capacity) float32 host outputs (pinned
+        CPU tensors for full speed).  Returns nnz."""
+        import torch
+        def host(t, dtype):
+            if isinstance(t, np.ndarray):
+                t = torch.from_numpy(t)
+            if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+                raise ValueError("host arrays must be contiguous CPU tensors / arrays of the stated dtype")
+            return t
+        t = host(tbme, torch.float32)
+        t2 = t if t.dim() == 2 else t.unsqueeze(0)
+        if t2.shape[1] != self.tbme_len:
+            raise ValueError("tbme must have tbme_len entries per set")
+        K = t2.shape[0]
+        rp, c, v = host(rowptr, torch.int64), host(col, torch.int32), host(val, torch.float32)
+        cap = c.numel()
+        if rp.numel() != self.dim + 1 or v.numel() != K * cap:
+            raise ValueError("rowptr needs dim + 1 entries and val K * capacity")
+        es = None if e_sp is None else host(torch.as_tensor(e_sp, dtype=torch.float64), torch.float64)
+        nnz = C.c_int64()
+        _ok(lib.cih_ham_build_host(self._h, K, float(hbar_omega), _ptr(t2), _ptr(es), _ptr(rp), _ptr(c), _ptr(v),
+                                   cap, C.byref(nnz), _stream(stream)), "ham_build_host")
+        return nnz.value
 
     def set_launch(self, warps_per_cta: int, ctas_per_sm: int = 0):
         """Launch shape of this basis' row kernels."""

@@ -19,11 +19,12 @@ struct Plan {
 // device memory of one wave, released in one place
 struct WaveMem {
     cudaStream_t st;
+    cudaMemPool_t pool;
     std::vector<void *> ptrs;
-    explicit WaveMem(cudaStream_t s) : st(s) {}
+    WaveMem(cudaStream_t s, cudaMemPool_t p) : st(s), pool(p) {}
     bool get(void **p, size_t bytes)
     {
-        if (cudaMallocAsync(p, std::max<size_t>(bytes, 16), st) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), pool, st) != cudaSuccess) {
             (void)cudaGetLastError();
             return false;
         }
@@ -138,7 +139,8 @@ int batch_solve(cih_instance_t *inst, int n, double hw, int nev, int max_iter, d
     }
 
     // 1. counts and row pointers of every instance
-    WaveMem keep(st);
+    const cudaMemPool_t pool = inst[0].basis->pool;
+    WaveMem keep(st, pool);
     std::vector<int64_t *> rowptr(n, nullptr);
     int64_t rowptr_bytes = 0;
     for (int i = 0; i < n; ++i) {
@@ -202,7 +204,7 @@ int batch_solve(cih_instance_t *inst, int n, double hw, int nev, int max_iter, d
 
     // 4. per wave: one graph of fills, then Lanczos and the adjoint per instance
     for (const std::vector<int> &w : waves) {
-        WaveMem mem(st);
+        WaveMem mem(st, pool);
         std::vector<int32_t *> col(n, nullptr);
         std::vector<float *> val(n, nullptr);
         std::vector<double *> psi(n, nullptr);
@@ -226,7 +228,7 @@ int batch_solve(cih_instance_t *inst, int n, double hw, int nev, int max_iter, d
             if (inst[i].grad_dev && b.layout.total > 0) {
                 const int64_t ng = (int64_t)inst[i].K * b.layout.total;
                 unsigned long long *acc = nullptr;
-                e = cudaMallocAsync((void **)&acc, sizeof(unsigned long long) * ng, st);
+                e = cudaMallocFromPoolAsync((void **)&acc, sizeof(unsigned long long) * ng, pool, st);
                 if (e != cudaSuccess) return fail(CIH_ERR_NOMEM, "batch: adjoint scratch");
                 e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * ng, st);
                 int g = e == cudaSuccess ? CIH_OK : cuda_fail(e, "batch: adjoint clear");

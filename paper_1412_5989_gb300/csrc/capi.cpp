@@ -268,6 +268,21 @@ int cih_ham_fill_batched(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, do
                        (cudaStream_t)stream);
 }
 
+int cih_ham_build_host(cih_basis_h h, int32_t K, double hbar_omega, const float *tbme_host, const double *e_sp_host,
+                       int64_t *rowptr_host, int32_t *col_host, float *val_host, int64_t capacity, int64_t *nnz_out,
+                       void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (K < 1 || K > 256 || !rowptr_host || !col_host || !val_host || capacity < 0 ||
+        (!tbme_host && h->layout.total > 0))
+        return fail(CIH_ERR_ARG, "build_host: K, host arrays or capacity");
+    return guarded([&]() -> int {
+        return build_host(*h, K, hbar_omega, tbme_host, e_sp_host, rowptr_host, col_host, val_host, capacity, nnz_out,
+                          (cudaStream_t)stream);
+    });
+}
+
 int cih_tbme_interleave(int32_t K, int64_t tbme_len, const float *tbme_dev, float *tbme_il_dev, void *stream)
 {
     if (K < 1 || tbme_len < 0 || (tbme_len > 0 && (!tbme_dev || !tbme_il_dev)))
@@ -386,7 +401,7 @@ int cih_ham_tbme_grad(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, const
     if (n == 0) return CIH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *acc = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&acc, sizeof(unsigned long long) * n, st);
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&acc, sizeof(unsigned long long) * n, h->pool, st);
     if (e != cudaSuccess) return fail(CIH_ERR_NOMEM, std::string("gradient scratch: ") + cudaGetErrorString(e));
     e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * n, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "gradient scratch clear");

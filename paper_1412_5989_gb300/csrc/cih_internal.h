@@ -211,7 +211,7 @@ int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
 int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
 // interleaved: tables element-major (len x K); em: values element-major (nnz x K)
 int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved, bool em,
-                const double *esp, int32_t *col, float *val, cudaStream_t st);
+                const double *esp, int32_t *col, float *val, cudaStream_t st, int64_t r0 = 0, int64_t r1 = -1);
 int launch_interleave(int K, int64_t len, const float *in, float *out, cudaStream_t st);
 // one-time set-up of the row kernels a call with K sets would launch (shared-
 // memory limits), so that launches made during a stream capture only launch
@@ -237,6 +237,10 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
             bool values_em = false);
 // device bytes lanczos() allocates for a call
 int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter);
+
+// tables from host memory, matrix to host memory, copies overlapped (host_io.cpp)
+int build_host(cih_basis &b, int K, double hw, const float *tbme_h, const double *esp_h, int64_t *rowptr_h,
+               int32_t *col_h, float *val_h, int64_t capacity, int64_t *nnz_out, cudaStream_t st);
 
 // count, admission, build, Lanczos and adjoint of a batch (batch.cpp)
 int batch_solve(cih_instance_t *inst, int n, double hw, int nev, int max_iter, double tol, int64_t budget,

@@ -389,7 +389,8 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
 
 template <int W, int MODE, bool K1, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
-k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs Gr, int *status)
+k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs Gr, int64_t r0, int64_t r1,
+       int *status)
 {
     constexpr int kThreads = WARPS * 32;
     extern __shared__ __align__(16) unsigned char sb[];
@@ -431,7 +432,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     // K sets, element-major values: warp-cooperative value writes
     const bool coop = MODE == 1 && !K1 && F.em && F.vec4 && ((F.K >> 2) > 32 ? (F.K >> 2) % 32 == 0 : 32 % (F.K >> 2) == 0);
 
-    for (int64_t row = gw; row < B.dim; row += nw) {
+    for (int64_t row = r0 + gw; row < r1; row += nw) {
         const int p = B.row_p[row];
         const int nbp = B.nb[p];
         const int64_t rbp = B.rowbase[p];
@@ -698,7 +699,7 @@ cudaError_t raise_smem_limit(const void *kern, int dev, int bytes)
 
 template <int MODE, int WARPS>
 int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, const FillArgs &F, const GradArgs &G,
-                  cudaStream_t st, bool dry)
+                  cudaStream_t st, bool dry, int64_t r0, int64_t r1)
 {
     const DevBasis &D = b.dev;
     const size_t smem = MODE == 0 ? (size_t)sm::S<WARPS> : smem_bytes<WARPS>(D.sp[0].n_orb * D.pn_G);
@@ -713,10 +714,10 @@ int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, co
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
         per_sm = std::max(per_sm, 1);
         if (b.launch_ctas > 0) per_sm = std::min(per_sm, b.launch_ctas);
-        const int64_t want = (b.dim + WARPS - 1) / WARPS;
+        const int64_t want = (r1 - r0 + WARPS - 1) / WARPS;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, want));
         count_launches(1);
-        kern<<<grid, WARPS * 32, smem, st>>>(D, rowptr, counts, F, G, b.dev_status);
+        kern<<<grid, WARPS * 32, smem, st>>>(D, rowptr, counts, F, G, r0, r1, b.dev_status);
         ee = cudaGetLastError();
         return ee == cudaSuccess ? CIH_OK : cuda_fail(ee, "row kernel launch");
     };
@@ -728,15 +729,16 @@ int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, co
 
 template <int MODE>
 int launch_rows(const cih_basis &b, const int64_t *rowptr, int64_t *counts, const FillArgs &F, const GradArgs &G,
-                cudaStream_t st, bool dry = false)
+                cudaStream_t st, bool dry = false, int64_t r0 = 0, int64_t r1 = -1)
 {
-    if (b.dim == 0) return CIH_OK;
+    if (r1 < 0) r1 = b.dim;
+    if (b.dim == 0 || (!dry && r1 <= r0)) return CIH_OK;
     const DevBasis &D = b.dev;
     if (D.pn_G > kGroupCap || D.A > kMaxA || D.A - 1 > 32)
         return fail(CIH_ERR_UNSUPPORTED, "more than 33 particles or pn groups above the row kernel's capacity");
     if (D.tbme_len > INT32_MAX) return fail(CIH_ERR_UNSUPPORTED, "two-body table above 2^31 entries");
-    return b.launch_warps == 8 ? launch_rows_w<MODE, 8>(b, rowptr, counts, F, G, st, dry)
-                               : launch_rows_w<MODE, 16>(b, rowptr, counts, F, G, st, dry);
+    return b.launch_warps == 8 ? launch_rows_w<MODE, 8>(b, rowptr, counts, F, G, st, dry, r0, r1)
+                               : launch_rows_w<MODE, 16>(b, rowptr, counts, F, G, st, dry, r0, r1);
 }
 
 // element-major copy of K set-major tables: out[t * K + k] = in[k * len + t]
@@ -768,12 +770,12 @@ int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st)
 }
 
 int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved,
-                bool em, const double *esp, int32_t *col, float *val, cudaStream_t st)
+                bool em, const double *esp, int32_t *col, float *val, cudaStream_t st, int64_t r0, int64_t r1)
 {
     const int vec4 = interleaved && K % 4 == 0 && ((uintptr_t)tbme & 15) == 0 && (!em || ((uintptr_t)val & 15) == 0);
     FillArgs F{K, hw, tbme, interleaved ? 1 : b.layout.total, interleaved ? (int64_t)K : 1, vec4, em && K > 1 ? 1 : 0,
                esp, col, val};
-    return launch_rows<1>(b, rowptr, nullptr, F, GradArgs{}, st);
+    return launch_rows<1>(b, rowptr, nullptr, F, GradArgs{}, st, false, r0, r1);
 }
 
 int prepare_rows(const cih_basis &b, int K)

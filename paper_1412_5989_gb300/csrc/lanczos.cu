@@ -332,7 +332,10 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
 
     std::vector<void *> bufs;
     auto alloc = [&](void **p, size_t bytes) -> bool {
-        if (cudaMallocAsync(p, std::max<size_t>(bytes, 16), st) != cudaSuccess) return false;
+        if (cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), b.pool, st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
         bufs.push_back(*p);
         return true;
     };
@@ -500,6 +503,7 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "lanczos");
     }
+    cudaMemPoolTrimTo(b.pool, 0);                            // the Lanczos vectors go back to the system
     return rc ? rc : not_converged;
 }
 

@@ -68,3 +68,34 @@ def test_batch_with_a_repeated_basis_and_two_sets(cih):
         assert conv
         np.testing.assert_array_equal(ev, o["evals"])
         assert torch.equal(B.tbme_grad(rowptr, psi), o["grad"])
+
+
+@pytest.mark.parametrize("K", [1, 3])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_build_to_host_matches_device_fill(cih, K, pinned):
+    """Host tables in, host matrix out (chunked fill with overlapped copies):
+    identical to the device-resident count + fill; a too small capacity is
+    refused with the count reported."""
+    sp = (3, 3, 4, 0)
+    B = cih.Basis(*sp)
+    T = synth.tbme_tables(B.tbme_len, range(20, 20 + K))
+    esp = synth.single_particle_energies(sum(B.n_orb), 5)
+    rowptr, nnz = B.count()
+    col, val = B.fill(rowptr, nnz, torch.from_numpy(T).cuda(), e_sp=torch.from_numpy(esp))
+    cap = nnz + 17
+    rp_h = torch.zeros(B.dim + 1, dtype=torch.int64, pin_memory=pinned)
+    col_h = torch.zeros(cap, dtype=torch.int32, pin_memory=pinned)
+    val_h = torch.zeros((K, cap), dtype=torch.float32, pin_memory=pinned)
+    tb_h = torch.from_numpy(T)
+    if pinned:
+        tb_h = tb_h.pin_memory()
+    n = B.build_to_host(tb_h, rp_h, col_h, val_h, e_sp=esp)
+    B.check()
+    assert n == nnz
+    assert torch.equal(rp_h, rowptr.cpu())
+    assert torch.equal(col_h[:nnz], col.cpu())
+    assert torch.equal(val_h[:, :nnz], val.cpu())
+    small = torch.zeros(nnz - 1, dtype=torch.int32)
+    with pytest.raises(cih.CihError) as e:
+        B.build_to_host(tb_h, rp_h, small, torch.zeros((K, nnz - 1), dtype=torch.float32))
+    assert e.value.code == -3
