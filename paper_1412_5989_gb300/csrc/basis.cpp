@@ -10,6 +10,7 @@
 // bucketed by (2M, parity, N) with a stable counting sort, which yields the
 // (2M, N mod 2, N, bits) order in linear time.
 #include <algorithm>
+#include <memory>
 #include <exception>
 #include <thread>
 #include <climits>
@@ -111,47 +112,100 @@ void parallel_tops(int ntop, Fn &&fn)
     for (auto &x : th) x.join();
 }
 
-void enumerate_subdets(Species &s)
-{
-    if (s.Z == 0) {                               // the empty sub-determinant
-        s.n_sd = 1;
-        s.bits.assign(kMaxWords, 0);
-        s.N.assign(1, 0);
-        s.M2.assign(1, 0);
-        return;
-    }
-    Timer tm("enumerate");
-    Enumerator E(s);
-    const int budget = s.Nsub_max;
+// The two passes of the enumeration, split so that the appearing filter can
+// run between them: after both species' count passes, a bucket (2M, N) of
+// one species appears when the other species has a non-empty bucket (2M',
+// N') with 2M + 2M' = 2M_total, N + N' <= Nlim and N + N' = Nlim (mod 2) (the
+// relation is symmetric, so the unfiltered counts decide it).  The write pass
+// then gives slots to the appearing buckets only.
+struct SubdetCount {
+    std::unique_ptr<Enumerator> E;
     std::vector<int> tops;
+    int64_t nk = 0;
+    std::vector<int64_t> cnt;        // [top][bucket]
+    std::vector<int64_t> total;      // per bucket
+    int M2_of(int64_t k) const { return 2 * (int)(k / E->nN) - E->Mabs; }
+    int N_of(int64_t k) const
+    {
+        const int r = (int)(k % E->nN), ne = (E->nN + 1) / 2;
+        return r < ne ? 2 * r : 2 * (r - ne) + 1;
+    }
+};
+
+void count_subdets(const Species &s, SubdetCount &C)
+{
+    if (s.Z == 0) return;                         // the empty sub-determinant: no passes
+    Timer tm("enumerate");
+    C.E.reset(new Enumerator(s));
+    const Enumerator &E = *C.E;
+    const int budget = s.Nsub_max;
     for (int a = s.Z - 1; a < s.n_orb; ++a)
-        if (s.oN[a] + E.minsum[s.Z - 1] <= budget) tops.push_back(a);
-    const int ntop = (int)tops.size();
-    const int64_t nk = E.nkeys();
-    std::vector<int64_t> cnt((size_t)ntop * nk, 0);        // [top][bucket]: one row per thread's top
+        if (s.oN[a] + E.minsum[s.Z - 1] <= budget) C.tops.push_back(a);
+    const int ntop = (int)C.tops.size();
+    C.nk = E.nkeys();
+    C.cnt.assign((size_t)ntop * C.nk, 0);          // one row per top: no shared counters
     parallel_tops(ntop, [&](int t) {
         uint64_t w[kMaxWords] = {0, 0, 0, 0};
-        const int a = tops[t];
+        const int a = C.tops[t];
         w[a >> 6] |= 1ull << (a & 63);
-        int64_t *c = &cnt[(size_t)t * nk];
+        int64_t *c = &C.cnt[(size_t)t * C.nk];
         auto f = [&](const uint64_t *, int N, int M) { c[E.key(N, M)]++; };
         E.rec(w, s.Z - 1, a, budget - s.oN[a], s.oN[a], s.om2[a], f);
     });
-    tm.mark("count pass");
-    // slots in (bucket, top) order
-    // slot of (top t, bucket k) = start of bucket k + counts of lower tops in k
-    std::vector<int64_t> run(nk, 0);
+    C.total.assign(C.nk, 0);
     for (int t = 0; t < ntop; ++t)
-        for (int64_t k = 0; k < nk; ++k) run[k] += cnt[(size_t)t * nk + k];
+        for (int64_t k = 0; k < C.nk; ++k) C.total[k] += C.cnt[(size_t)t * C.nk + k];
+    tm.mark("count pass");
+}
+
+// (2M, N) of the non-empty buckets of a species (the empty sub-determinant
+// when it has no particles)
+std::vector<std::pair<int, int>> filled_buckets(const Species &s, const SubdetCount &C)
+{
+    std::vector<std::pair<int, int>> v;
+    if (s.Z == 0) { v.push_back({0, 0}); return v; }
+    for (int64_t k = 0; k < C.nk; ++k)
+        if (C.total[k] > 0) v.push_back({C.M2_of(k), C.N_of(k)});
+    return v;
+}
+
+// which (2M, N) of this species pair with some filled bucket of the other
+bool appears(int M2, int N, int twoM, int Nlim, const std::vector<int> &minN, int mspan)
+{
+    const int room = Nlim - N, mo = twoM - M2;
+    if (room < 0 || mo < -mspan || mo > mspan) return false;
+    return minN[(size_t)(mo + mspan) * 2 + (room & 1)] <= room;
+}
+
+void write_subdets(Species &s, SubdetCount &C, const std::vector<char> &keep_key)
+{
+    if (s.Z == 0) {                               // the empty sub-determinant
+        s.n_sd = keep_key.empty() || keep_key[0] ? 1 : 0;
+        s.bits.assign((size_t)s.n_sd * kMaxWords, 0);
+        s.N.assign(s.n_sd, 0);
+        s.M2.assign(s.n_sd, 0);
+        return;
+    }
+    Timer tm("enumerate");
+    const Enumerator &E = *C.E;
+    const int budget = s.Nsub_max;
+    const int ntop = (int)C.tops.size();
+    const int64_t nk = C.nk;
+    // slots in (bucket, top) order over the kept buckets; a dropped bucket's
+    // slots are -1 and its sub-determinants are not written
+    std::vector<int64_t> run(nk, 0);
     int64_t total = 0;
-    for (int64_t k = 0; k < nk; ++k) { const int64_t v = run[k]; run[k] = total; total += v; }
+    for (int64_t k = 0; k < nk; ++k) {
+        run[k] = total;
+        if (keep_key[k]) total += C.total[k];
+    }
     for (int t = 0; t < ntop; ++t)
         for (int64_t k = 0; k < nk; ++k) {
-            const int64_t v = cnt[(size_t)t * nk + k];
-            cnt[(size_t)t * nk + k] = run[k];
+            int64_t &c = C.cnt[(size_t)t * nk + k];
+            const int64_t v = c;
+            c = keep_key[k] ? run[k] : -1;
             run[k] += v;
         }
-    run.assign(1, total);
     tm.mark("prefix");
     s.n_sd = total;
     s.bits.assign((size_t)total * kMaxWords, 0);
@@ -159,11 +213,13 @@ void enumerate_subdets(Species &s)
     s.M2.assign(total, 0);
     parallel_tops(ntop, [&](int t) {
         uint64_t w[kMaxWords] = {0, 0, 0, 0};
-        const int a = tops[t];
+        const int a = C.tops[t];
         w[a >> 6] |= 1ull << (a & 63);
-        int64_t *slot = &cnt[(size_t)t * nk];
+        int64_t *slot = &C.cnt[(size_t)t * nk];
         auto f = [&](const uint64_t *wb, int N, int M) {
-            const int64_t i = slot[E.key(N, M)]++;
+            int64_t &sl = slot[E.key(N, M)];
+            if (sl < 0) return;
+            const int64_t i = sl++;
             std::copy(wb, wb + kMaxWords, &s.bits[(size_t)i * kMaxWords]);
             s.N[i] = N;
             s.M2[i] = M;
@@ -172,45 +228,7 @@ void enumerate_subdets(Species &s)
     });
 }
 
-void keep_only(Species &s, const std::vector<char> &keep)
-{
-    int64_t k = 0;
-    for (int64_t i = 0; i < s.n_sd; ++i) {
-        if (!keep[i]) continue;
-        if (k != i) {
-            std::copy(&s.bits[i * kMaxWords], &s.bits[i * kMaxWords] + kMaxWords, &s.bits[k * kMaxWords]);
-            s.N[k] = s.N[i];
-            s.M2[k] = s.M2[i];
-        }
-        ++k;
-    }
-    s.n_sd = k;
-    s.bits.resize((size_t)k * kMaxWords);
-    s.N.resize(k);
-    s.M2.resize(k);
-}
 
-// f0() here and f1() on a second thread; an exception of either is rethrown
-template <class F0, class F1>
-void side_by_side(F0 &&f0, F1 &&f1)
-{
-    std::exception_ptr e1;
-    std::thread th([&]() {
-        try {
-            f1();
-        } catch (...) {
-            e1 = std::current_exception();
-        }
-    });
-    try {
-        f0();
-    } catch (...) {
-        th.join();
-        throw;
-    }
-    th.join();
-    if (e1) std::rethrow_exception(e1);
-}
 
 void make_classes(Species &s)
 {
@@ -356,36 +374,38 @@ int build_host_species(const cih_space_t &sp, cih_basis &b)
         b.s[t].Nsub_max = b.Nlim - b.s[1 - t].N0;
         words = std::max(words, (b.s[t].n_orb + 63) / 64);
     }
-    // the two species are independent: enumerate them side by side
-    side_by_side([&]() { enumerate_subdets(b.s[0]); }, [&]() { enumerate_subdets(b.s[1]); });
-    tm.mark("enumerate p and n");
     b.W = words <= 1 ? 1 : words <= 2 ? 2 : 4;
-    tm.mark("enumerate + bucket sort");
 
-    // appearing sub-dets: x pairs with some y of the other species when the
-    // lowest-N partner of the right (2M, parity) fits under Nlim
+    // the two species are independent: count them side by side
+    SubdetCount cnt[2];
+    side_by_side([&]() { count_subdets(b.s[0], cnt[0]); }, [&]() { count_subdets(b.s[1], cnt[1]); });
+    tm.mark("count p and n");
+
+    // appearing buckets: those with a partner bucket of the other species
+    std::vector<char> keep[2];
     for (int t = 0; t < 2; ++t) {
-        const Species &o = b.s[1 - t];
-        Species &s = b.s[t];
+        const std::vector<std::pair<int, int>> mine = filled_buckets(b.s[t], cnt[t]);
+        const std::vector<std::pair<int, int>> other = filled_buckets(b.s[1 - t], cnt[1 - t]);
         int mspan = std::abs(sp.twoM);
-        for (int64_t i = 0; i < o.n_sd; ++i) mspan = std::max(mspan, std::abs(o.M2[i]));
-        for (int64_t i = 0; i < s.n_sd; ++i) mspan = std::max(mspan, std::abs(s.M2[i]) + std::abs(sp.twoM));
+        for (const auto &q : other) mspan = std::max(mspan, std::abs(q.first));
+        for (const auto &q : mine) mspan = std::max(mspan, std::abs(q.first) + std::abs(sp.twoM));
         std::vector<int> minN((size_t)(2 * mspan + 1) * 2, INT_MAX);   // (2M + mspan) * 2 + parity
-        for (int64_t i = 0; i < o.n_sd; ++i) {
-            int &m = minN[(size_t)(o.M2[i] + mspan) * 2 + (o.N[i] & 1)];
-            m = std::min(m, o.N[i]);
+        for (const auto &q : other) {
+            int &m = minN[(size_t)(q.first + mspan) * 2 + (q.second & 1)];
+            m = std::min(m, q.second);
         }
-        std::vector<char> keep(s.n_sd, 0);
-        for (int64_t i = 0; i < s.n_sd; ++i) {
-            int room = b.Nlim - s.N[i];
-            int mo = sp.twoM - s.M2[i];
-            if (room < 0 || mo < -mspan || mo > mspan) continue;
-            keep[i] = minN[(size_t)(mo + mspan) * 2 + (room & 1)] <= room;
+        if (b.s[t].Z == 0) {
+            keep[t].assign(1, appears(0, 0, sp.twoM, b.Nlim, minN, mspan) ? 1 : 0);
+        } else {
+            keep[t].assign(cnt[t].nk, 0);
+            for (int64_t k = 0; k < cnt[t].nk; ++k)
+                keep[t][k] = cnt[t].total[k] > 0 &&
+                             appears(cnt[t].M2_of(k), cnt[t].N_of(k), sp.twoM, b.Nlim, minN, mspan);
         }
-        keep_only(s, keep);
     }
-    // the filter of the second species used the first one's filtered list;
-    // pairing is symmetric, so the first species' list is still exact.
+    side_by_side([&]() { write_subdets(b.s[0], cnt[0], keep[0]); },
+                 [&]() { write_subdets(b.s[1], cnt[1], keep[1]); });
+    tm.mark("appearing sub-dets written");
     side_by_side([&]() { make_classes(b.s[0]); }, [&]() { make_classes(b.s[1]); });
     tm.mark("appearing filter + classes");
     return CIH_OK;

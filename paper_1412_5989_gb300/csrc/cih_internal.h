@@ -3,7 +3,9 @@
 
 #include <cstdint>
 #include <string>
+#include <exception>
 #include <functional>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -173,6 +175,28 @@ struct cih_basis {
 };
 
 namespace cih {
+
+// f0() here and f1() on a second thread; an exception of either is rethrown
+template <class F0, class F1>
+inline void side_by_side(F0 &&f0, F1 &&f1)
+{
+    std::exception_ptr e1;
+    std::thread th([&]() {
+        try {
+            f1();
+        } catch (...) {
+            e1 = std::current_exception();
+        }
+    });
+    try {
+        f0();
+    } catch (...) {
+        th.join();
+        throw;
+    }
+    th.join();
+    if (e1) std::rethrow_exception(e1);
+}
 
 // every kernel launch site adds the launches it makes (capi.cpp)
 void count_launches(int64_t n);

@@ -754,38 +754,52 @@ int lists_phase3(cih_basis &b, int t, SpeciesBuild &S, Lists &L, cudaStream_t st
     return CIH_OK;
 }
 
-// species t: host arrays, their upload and the one-move hash table
-int species_upload(cih_basis &b, int t, cudaStream_t st)
+// species t: host arrays (built for both species side by side), then their
+// upload and the one-move hash table
+struct SpeciesHost {
+    std::vector<uint64_t> bits;
+    std::vector<int8_t> N, oN;
+    std::vector<int16_t> M2, om2;
+    std::vector<int32_t> cls_end, lookup, cb, ce;
+    int moff = 0, mspan = 0;
+};
+
+void species_prep(const cih_basis &b, int t, SpeciesHost &H)
+{
+    const int W = b.W;
+    const Species &s = b.s[t];
+    H.bits.resize((size_t)s.n_sd * W);               // bit strings compacted to W words
+    for (int64_t i = 0; i < s.n_sd; ++i)
+        for (int w = 0; w < W; ++w) H.bits[i * W + w] = s.bits[i * kMaxWords + w];
+    H.N.assign(s.N.begin(), s.N.end());
+    H.M2.assign(s.M2.begin(), s.M2.end());
+    H.cls_end.resize(s.n_sd);
+    for (int64_t i = 0; i < s.n_sd; ++i) H.cls_end[i] = s.cls_end[s.cls[i]];
+    int mabs = 0;
+    for (int m : s.cls_M2) mabs = std::max(mabs, std::abs(m));
+    H.mspan = 2 * mabs + 1 + 64;                     // room for moves that leave the table
+    H.moff = mabs + 32;
+    H.lookup.assign((size_t)H.mspan * 2, -1);
+    for (size_t c = 0; c < s.cls_begin.size(); ++c)
+        H.lookup[(size_t)(s.cls_M2[c] + H.moff) * 2 + s.cls_par[c]] = (int32_t)c;
+    H.cb.assign(s.cls_begin.begin(), s.cls_begin.end());
+    H.ce.assign(s.cls_end.begin(), s.cls_end.end());
+    H.oN.assign(s.oN.begin(), s.oN.end());
+    H.om2.assign(s.om2.begin(), s.om2.end());
+}
+
+int species_upload(cih_basis &b, int t, const SpeciesHost &H, cudaStream_t st)
 {
     const int W = b.W;
     const Species &s = b.s[t];
     int rc;
-    // bit strings compacted to W words
-    std::vector<uint64_t> bits((size_t)s.n_sd * W);
-    for (int64_t i = 0; i < s.n_sd; ++i)
-        for (int w = 0; w < W; ++w) bits[i * W + w] = s.bits[i * kMaxWords + w];
-    std::vector<int8_t> N(s.N.begin(), s.N.end());
-    std::vector<int16_t> M2(s.M2.begin(), s.M2.end());
-    std::vector<int32_t> cls_end(s.n_sd);
-    for (int64_t i = 0; i < s.n_sd; ++i) cls_end[i] = s.cls_end[s.cls[i]];
-    int mabs = 0;
-    for (int m : s.cls_M2) mabs = std::max(mabs, std::abs(m));
-    int mspan = 2 * mabs + 1 + 64;          // room for moves that leave the table
-    int moff = mabs + 32;
-    std::vector<int32_t> lookup((size_t)mspan * 2, -1);
-    for (size_t c = 0; c < s.cls_begin.size(); ++c)
-        lookup[(size_t)(s.cls_M2[c] + moff) * 2 + s.cls_par[c]] = (int32_t)c;
-    std::vector<int32_t> cb(s.cls_begin.begin(), s.cls_begin.end()), ce(s.cls_end.begin(), s.cls_end.end());
-    std::vector<int8_t> oN(s.oN.begin(), s.oN.end());
-    std::vector<int16_t> om2(s.om2.begin(), s.om2.end());
-
     uint64_t *d_bits; int8_t *d_N; int16_t *d_M2; int32_t *d_cls_end, *d_lookup, *d_cb, *d_ce;
     int8_t *d_oN; int16_t *d_om2;
-    if ((rc = upload(b, &d_bits, bits, st)) || (rc = upload(b, &d_N, N, st)) ||
-        (rc = upload(b, &d_M2, M2, st)) || (rc = upload(b, &d_cls_end, cls_end, st)) ||
-        (rc = upload(b, &d_lookup, lookup, st)) || (rc = upload(b, &d_cb, cb, st)) ||
-        (rc = upload(b, &d_ce, ce, st)) || (rc = upload(b, &d_oN, oN, st)) ||
-        (rc = upload(b, &d_om2, om2, st)))
+    if ((rc = upload(b, &d_bits, H.bits, st)) || (rc = upload(b, &d_N, H.N, st)) ||
+        (rc = upload(b, &d_M2, H.M2, st)) || (rc = upload(b, &d_cls_end, H.cls_end, st)) ||
+        (rc = upload(b, &d_lookup, H.lookup, st)) || (rc = upload(b, &d_cb, H.cb, st)) ||
+        (rc = upload(b, &d_ce, H.ce, st)) || (rc = upload(b, &d_oN, H.oN, st)) ||
+        (rc = upload(b, &d_om2, H.om2, st)))
         return rc;
     DevSpecies &D = b.dev.sp[t];
     D.bits = d_bits;
@@ -796,7 +810,7 @@ int species_upload(cih_basis &b, int t, cudaStream_t st)
     D.orb_base = t == 0 ? 0 : b.s[0].n_orb;
 
     SpeciesBuild S{d_bits, d_N, d_M2, d_cls_end, d_lookup, d_cb, d_ce, d_oN, d_om2,
-                   (int32_t)s.n_sd, s.n_orb, moff, mspan, s.Nsub_max, nullptr, 0};
+                   (int32_t)s.n_sd, s.n_orb, H.moff, H.mspan, s.Nsub_max, nullptr, 0};
     uint32_t cap = 64;
     while (cap < 2 * (uint64_t)s.n_sd) cap <<= 1;
     int32_t *table;
@@ -878,9 +892,16 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
     Lists L[2];
     L[0].tot = pin.p;
     L[1].tot = pin.p + 3;
+    // every kernel reads W words per bit string: they must hold every orbital
+    for (int t = 0; t < 2; ++t)
+        if (64 * W < b.s[t].n_orb || (W != 1 && W != 2 && W != 4))
+            return fail(CIH_ERR_UNSUPPORTED, "internal: bit strings of " + std::to_string(W) + " words for " +
+                                                 std::to_string(b.s[t].n_orb) + " orbitals");
     // 1. per species: upload, hash table, staged passes (queued, no synchronisation)
+    SpeciesHost H[2];
+    side_by_side([&]() { species_prep(b, 0, H[0]); }, [&]() { species_prep(b, 1, H[1]); });
     for (int t = 0; t < 2; ++t) {
-        if ((rc = species_upload(b, t, st))) return rc;
+        if ((rc = species_upload(b, t, H[t], st))) return rc;
         if (W == 1) rc = lists_phase1<1>(b, t, b.sbuild[t], L[t], st);
         else if (W == 2) rc = lists_phase1<2>(b, t, b.sbuild[t], L[t], st);
         else rc = lists_phase1<4>(b, t, b.sbuild[t], L[t], st);
