@@ -23,6 +23,7 @@
 // spectators k in R in ascending combined order.  Proton and neutron moves
 // of a pn element factorise (the cross-species counts cancel in pairs).
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 
@@ -60,6 +61,7 @@ constexpr double kFixScale = 72057594037927936.0;   // 2^56
 // The group sizes and offsets come from shared memory (lg: size and offset
 // per group, int2) when the layout has at most kLayoutCap groups.
 constexpr int kLayoutCap = 512;
+constexpr int kOrbCap = 512;      // combined orbitals (two species of at most 256)
 __device__ __forceinline__ bool tbme_at(const DevBasis &B, const int2 *lg, int a, int b, int c, int d, int64_t &idx,
                                         int &sign)
 {
@@ -117,7 +119,8 @@ constexpr int goff = gsize + kGroupCap * 4;                // int32[kGroupCap]
 constexpr int pi = goff + kGroupCap * 4;                   // uint8[kPairCap]
 constexpr int pj = pi + kPairCap;                          // uint8[kPairCap]
 constexpr int lg = (pj + kPairCap + 15) / 16 * 16;         // int2[kLayoutCap]: table group size, offset
-constexpr int warp0 = lg + kLayoutCap * 8;
+constexpr int e1 = lg + kLayoutCap * 8;                    // float2[kOrbCap]: one-body energies, hi + lo
+constexpr int warp0 = e1 + kOrbCap * 8;
 // per warp
 constexpr int w_seg = 0;                                   // int4[64]: colbase, uv, mv, row start
 constexpr int w_ext = w_seg + 64 * 16;                     // int2[64]: list start, insertion point
@@ -143,13 +146,38 @@ __device__ __forceinline__ double warp_sum(double v, int width)
     return v;
 }
 
-// table index of a pn element from the candidate (uv, mv) and neutron move (ni)
-template <int WARPS>
-__device__ __forceinline__ int pn_index(const unsigned char *sb, uint32_t uv, uint32_t mv, uint32_t ni, int &sign)
+// A sum of FP32 terms carried as the unevaluated pair hi + lo of floats
+// (Dekker's two-sum), about 48 significant bits: exact for the value sums here
+// (at most a few dozen FP32 terms within 24 binary orders of magnitude), and
+// single-precision arithmetic runs at full rate where the GPU's FP64 units are
+// few.  The value stored is hi + lo rounded once to FP32.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b)
 {
-    const int16_t *S = reinterpret_cast<const int16_t *>(sb + sm::S<WARPS>);
-    const int32_t *gs = reinterpret_cast<const int32_t *>(sb + sm::gsize);
-    const int32_t *go = reinterpret_cast<const int32_t *>(sb + sm::goff);
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = (e + a.lo) + b.lo;
+    const float hi = s + lo;
+    return DF{hi, lo - (hi - s)};
+}
+__device__ __forceinline__ DF df_of(float x) { return DF{x, 0.f}; }
+__device__ __forceinline__ float df_round(DF v) { return v.hi + v.lo; }
+__device__ __forceinline__ DF warp_sum(DF v, int width)
+{
+    for (int d = width >> 1; d > 0; d >>= 1) {
+        const DF o{__shfl_xor_sync(0xffffffffu, v.hi, d, width), __shfl_xor_sync(0xffffffffu, v.lo, d, width)};
+        v = df_add(v, o);
+    }
+    return v;
+}
+
+// table index of a pn element from the candidate (uv, mv) and neutron move (ni)
+__device__ __forceinline__ int pn_index_at(const int16_t *S, const int32_t *gs, const int32_t *go, uint32_t uv,
+                                           uint32_t mv, uint32_t ni, int &sign)
+{
     const int t = (int)((ni >> 16) & 0x7F) - 64 + (int)(((mv >> 8) ^ (ni >> 23)) & 1);
     const int kappa = (int)(mv & 0xFF) + t;
     int u = S[(int)(uv & 0xFFFF) + t] + (int)((ni >> 8) & 0xFF);
@@ -157,6 +185,14 @@ __device__ __forceinline__ int pn_index(const unsigned char *sb, uint32_t uv, ui
     if (u > v) { const int x = u; u = v; v = x; }
     sign = (int)(((mv >> 9) ^ (ni >> 24)) & 1);
     return go[kappa] + u * gs[kappa] - ((u * (u - 1)) >> 1) + (v - u);
+}
+
+template <int WARPS>
+__device__ __forceinline__ int pn_index(const unsigned char *sb, uint32_t uv, uint32_t mv, uint32_t ni, int &sign)
+{
+    return pn_index_at(reinterpret_cast<const int16_t *>(sb + sm::S<WARPS>),
+                       reinterpret_cast<const int32_t *>(sb + sm::gsize),
+                       reinterpret_cast<const int32_t *>(sb + sm::goff), uv, mv, ni, sign);
 }
 
 // Row output view: column and value pointers at the row's first element;
@@ -329,12 +365,15 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
             __syncwarp();
             const int eo = w_spos[e];
             for (int k = lane; k < F.K; k += 32) {
-                double v = 0.0;
+                DF v = df_of(0.f);
                 for (int i = 0; i < sp_n; ++i) {
                     const int2 q = spec[i];
-                    if (q.x >= 0) v += q.y * (double)__ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)q.x * F.tb_si);
+                    if (q.x < 0) continue;
+                    const float t = __ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)q.x * F.tb_si);
+                    v = df_add(v, df_of(q.y < 0 ? -t : t));
                 }
-                R.val[(int64_t)eo * R.es + (int64_t)k * R.ks] = (float)(sgn ? -v : v);
+                const float r = df_round(v);
+                R.val[(int64_t)eo * R.es + (int64_t)k * R.ks] = sgn ? -r : r;
             }
             if (lane == 0) R.col[eo] = w_scol[e];
             __syncwarp();
@@ -369,12 +408,16 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
         }
         for (int kk = 0; kk < (MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++kk) {
             if (MODE == 1) {
-                double v = 0.0;
-                if (has && ok) v = sg * (double)__ldg(F.tbme + (int64_t)kk * F.tb_sk + idx * F.tb_si);
+                DF v = df_of(0.f);
+                if (has && ok) {
+                    const float t = __ldg(F.tbme + (int64_t)kk * F.tb_sk + idx * F.tb_si);
+                    v = df_of(sg < 0 ? -t : t);
+                }
                 v = warp_sum(v, gsz);
                 if (act && i == 0) {
                     if (kk == 0) R.col[eo] = (int32_t)colj;
-                    R.val[(int64_t)eo * R.es + (int64_t)kk * R.ks] = (float)(sgn ? -v : v);
+                    const float r = df_round(v);
+                    R.val[(int64_t)eo * R.es + (int64_t)kk * R.ks] = sgn ? -r : r;
                 }
             } else if (has && ok) {
                 const double f = 2.0 * Gr.psi[(int64_t)kk * B.dim + R.row] * Gr.psi[(int64_t)kk * B.dim + colj];
@@ -408,6 +451,14 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         if (B.ngroups <= kLayoutCap) {
             int2 *lgw = sptr<int2>(sb, sm::lg);
             for (int g = tid; g < B.ngroups; g += kThreads) lgw[g] = make_int2(B.gsize[g], (int)B.goff[g]);
+        }
+        if (MODE == 1) {                                   // one-body energies as hi + lo pairs
+            float2 *e1w = sptr<float2>(sb, sm::e1);
+            for (int a = tid; a < B.ntot && a < kOrbCap; a += kThreads) {
+                const double e = F.esp ? F.esp[a] : F.hw * ((double)B.orbN[a] + 1.5);
+                const float hi = (float)e;
+                e1w[a] = make_float2(hi, (float)(e - (double)hi));
+            }
         }
         uint8_t *pi = sptr<uint8_t>(sb, sm::pi), *pj = sptr<uint8_t>(sb, sm::pj);
         for (int l = tid; l < npairs; l += kThreads) {     // pair l -> (i, j), i < j
@@ -473,26 +524,27 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     w_scode[l] = sg < 0 ? 1u : 0u;
                 }
                 __syncwarp();
-                double one = 0.0;
+                DF one = df_of(0.f);
+                const float2 *e1 = sptr<float2>(sb, sm::e1);
                 for (int i = 0; i < A; ++i) {
-                    const int a = w_occ[i];
-                    one += F.esp ? F.esp[a] : F.hw * ((double)B.orbN[a] + 1.5);
+                    const float2 q = e1[w_occ[i]];
+                    one = df_add(one, DF{q.x, q.y});
                 }
                 for (int k = lane; k < F.K; k += 32) {
-                    double acc = 0.0;
+                    DF acc = df_of(0.f);
                     for (int l = 0; l < npairs; ++l) {
                         const int32_t idx = w_scol[l];
                         if (idx < 0) continue;
-                        const double v = (double)__ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)idx * F.tb_si);
-                        acc += w_scode[l] ? -v : v;
+                        const float v = __ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)idx * F.tb_si);
+                        acc = df_add(acc, df_of(w_scode[l] ? -v : v));
                     }
-                    if (rowlen > 0) R.val[(int64_t)k * R.ks] = (float)(acc + one);
+                    if (rowlen > 0) R.val[(int64_t)k * R.ks] = df_round(df_add(acc, one));
                 }
                 if (lane == 0 && rowlen > 0) R.col[0] = (int32_t)row;
                 __syncwarp();
             }
             for (int k = 0; k < (kset ? 0 : MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++k) {
-                double acc = 0.0;
+                DF acc = df_of(0.f);
                 for (int l = lane; l < npairs; l += 32) {
                     const int a = w_occ[pi[l]], c = w_occ[pj[l]];
                     int64_t idx;
@@ -502,7 +554,8 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                         continue;
                     }
                     if (MODE == 1) {
-                        acc += sg * (double)__ldg(F.tbme + (int64_t)k * F.tb_sk + idx * F.tb_si);
+                        const float v = __ldg(F.tbme + (int64_t)k * F.tb_sk + idx * F.tb_si);
+                        acc = df_add(acc, df_of(sg < 0 ? -v : v));
                     } else {
                         const double pr = Gr.psi[(int64_t)k * B.dim + row];
                         const long long qv = __double2ll_rn(sg * pr * pr * kFixScale);
@@ -510,14 +563,15 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     }
                 }
                 if (MODE == 1) {
+                    const float2 *e1 = sptr<float2>(sb, sm::e1);
                     for (int i = lane; i < A; i += 32) {
-                        const int a = w_occ[i];
-                        acc += F.esp ? F.esp[a] : F.hw * ((double)B.orbN[a] + 1.5);
+                        const float2 q = e1[w_occ[i]];
+                        acc = df_add(acc, DF{q.x, q.y});
                     }
                     acc = warp_sum(acc, 32);
                     if (lane == 0 && rowlen > 0) {
                         if (k == 0) R.col[0] = (int32_t)row;
-                        R.val[(int64_t)k * R.ks] = (float)acc;
+                        R.val[(int64_t)k * R.ks] = df_round(acc);
                     }
                 }
             }
