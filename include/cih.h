@@ -235,12 +235,16 @@ int cih_lanczos_lowest_em(cih_basis_h h, const int64_t *rowptr_dev, const int32_
 /* Adjoint: d E0 / d t for every two-body table entry t of each of K sets,
  * given the normalised lowest eigenvectors psi (Hellmann-Feynman, E0 =
  * psi^T H psi): g_t = sum over stored (i, j) whose value uses t with sign s of
- * w * s * psi_i * psi_j, w = 2 off the diagonal and 1 on it.  The sum is
- * deterministic (fixed-point integer accumulation, 2^-56 resolution).
- *   psi_dev: K x dim double (device); grad_dev: K x tbme_len double (device,
- *   caller-owned, overwritten).
- * Scratch: K x tbme_len int64 library-allocated for the call.
- * Errors: CIH_ERR_ARG, CIH_ERR_NOMEM, CIH_ERR_CUDA. */
+ * w * s * psi_i * psi_j, w = 2 off the diagonal and 1 on it.  Integer
+ * arithmetic throughout, so the sum is deterministic: psi is held as
+ * psi_i * 2^61 (int64), each product psi_i psi_j as the high word of the
+ * 128-bit product (2^-58 units), and g accumulates in 2^-56 units.
+ *   psi_dev: K x dim double (device), |psi_i| < 4 (a normalised vector
+ *   qualifies; a larger entry sets the device status that cih_check reports
+ *   and counts as 0); grad_dev: K x tbme_len double (device, caller-owned,
+ *   overwritten).
+ * Scratch: K x tbme_len int64 and K x dim int64, library-allocated for the
+ * call.  Errors: CIH_ERR_ARG, CIH_ERR_NOMEM, CIH_ERR_CUDA. */
 int cih_ham_tbme_grad(cih_basis_h h, const int64_t *rowptr_dev, int32_t K,
                       const double *psi_dev, double *grad_dev, void *stream);
 

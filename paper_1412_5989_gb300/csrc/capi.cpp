@@ -356,7 +356,7 @@ int cih_check(cih_basis_h h, void *stream)
     if (status)
         return fail(CIH_ERR_DEVICE, std::string("device status bits ") + std::to_string(status) +
                                         " (1: pair outside the table layout, 2: write beyond the row, "
-                                        "4: two-move index, 8: deferred queue); first: " + std::to_string(st4[2]) + " " +
+                                        "4: two-move index, 8: deferred queue, 32: adjoint vector entry of magnitude 4 or more); first: " + std::to_string(st4[2]) + " " +
                                         std::to_string(st4[3]));
     return CIH_OK;
 }

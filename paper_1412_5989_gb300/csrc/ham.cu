@@ -50,11 +50,19 @@ struct FillArgs {
 
 struct GradArgs {
     int K;
-    const double *psi;        // K x dim
-    unsigned long long *acc;  // K x tbme_len fixed point
+    const long long *psi;     // K x dim, psi_i * 2^61 rounded (|psi_i| < 4)
+    unsigned long long *acc;  // K x tbme_len fixed point, 2^56 units
 };
 
 constexpr double kFixScale = 72057594037927936.0;   // 2^56
+constexpr double kPsiScale = 2305843009213693952.0;  // 2^61
+
+// psi_i psi_j in units of 2^-58: the high 64 bits of the 128-bit product of
+// the two 2^61-scaled vectors (integer arithmetic, exact but for the floor)
+__device__ __forceinline__ long long psi_prod(const long long *psi, int64_t i, int64_t j)
+{
+    return __mul64hi(psi[i], psi[j]);
+}
 
 // Table index of V(ab, cd) for combined orbitals in any order; false if the
 // pairs are not one table entry (a bug in the walk: flagged by the caller).
@@ -266,11 +274,9 @@ __device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F,
             }
         }
     } else if (MODE == 2) {
-        for (int k = 0; k < Gr.K; ++k) {
-            const double *psi = Gr.psi + (int64_t)k * B.dim;
-            const double f = 2.0 * psi[R.row] * psi[colj];
-            const long long qv = __double2ll_rn((sgn ? -f : f) * kFixScale);
-            atomicAdd(Gr.acc + (int64_t)k * B.tbme_len + idx, (unsigned long long)qv);
+        for (int k = 0; k < Gr.K; ++k) {                         // w psi_i psi_j, w = 2: 2^-57 units
+            const long long q = psi_prod(Gr.psi + (int64_t)k * B.dim, R.row, colj) >> 1;
+            atomicAdd(Gr.acc + (int64_t)k * B.tbme_len + idx, (unsigned long long)(sgn ? -q : q));
         }
     }
 }
@@ -420,9 +426,9 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
                     R.val[(int64_t)eo * R.es + (int64_t)kk * R.ks] = sgn ? -r : r;
                 }
             } else if (has && ok) {
-                const double f = 2.0 * Gr.psi[(int64_t)kk * B.dim + R.row] * Gr.psi[(int64_t)kk * B.dim + colj];
-                const long long qv = __double2ll_rn((sgn ? -1 : 1) * sg * f * kFixScale);
-                atomicAdd(Gr.acc + (int64_t)kk * B.tbme_len + idx, (unsigned long long)qv);
+                const long long q = psi_prod(Gr.psi + (int64_t)kk * B.dim, R.row, colj) >> 1;
+                const bool neg = (sgn != 0) != (sg < 0);
+                atomicAdd(Gr.acc + (int64_t)kk * B.tbme_len + idx, (unsigned long long)(neg ? -q : q));
             }
         }
     }
@@ -556,10 +562,9 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     if (MODE == 1) {
                         const float v = __ldg(F.tbme + (int64_t)k * F.tb_sk + idx * F.tb_si);
                         acc = df_add(acc, df_of(sg < 0 ? -v : v));
-                    } else {
-                        const double pr = Gr.psi[(int64_t)k * B.dim + row];
-                        const long long qv = __double2ll_rn(sg * pr * pr * kFixScale);
-                        atomicAdd(Gr.acc + (int64_t)k * B.tbme_len + idx, (unsigned long long)qv);
+                    } else {                                     // w = 1 on the diagonal
+                        const long long q = psi_prod(Gr.psi + (int64_t)k * B.dim, row, row) >> 2;
+                        atomicAdd(Gr.acc + (int64_t)k * B.tbme_len + idx, (unsigned long long)(sg < 0 ? -q : q));
                     }
                 }
                 if (MODE == 1) {
@@ -854,11 +859,37 @@ int launch_interleave(int K, int64_t len, const float *in, float *out, cudaStrea
     return e == cudaSuccess ? CIH_OK : cuda_fail(e, "interleave");
 }
 
+// psi_fix[i] = psi[i] * 2^61 rounded; |psi| >= 4 cannot be held and sets status bit 32
+__global__ void k_psi_fix(int64_t n, const double *psi, long long *psi_fix, int *status)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = psi[i];
+        if (!(fabs(v) < 4.0)) {
+            atomicOr(status, 32);
+            psi_fix[i] = 0;
+        } else {
+            psi_fix[i] = __double2ll_rn(v * kPsiScale);
+        }
+    }
+}
+
 int launch_grad(const cih_basis &b, const int64_t *rowptr, int K, const double *psi,
                 unsigned long long *acc, cudaStream_t st)
 {
-    GradArgs G{K, psi, acc};
-    return launch_rows<2>(b, rowptr, nullptr, FillArgs{}, G, st);
+    const int64_t n = (int64_t)K * b.dim;
+    if (n == 0) return CIH_OK;
+    long long *fix = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&fix, sizeof(long long) * n, b.pool, st);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(CIH_ERR_NOMEM, "adjoint: fixed-point vector");
+    }
+    count_launches(1);
+    k_psi_fix<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(n, psi, fix, b.dev_status);
+    GradArgs G{K, fix, acc};
+    const int rc = launch_rows<2>(b, rowptr, nullptr, FillArgs{}, G, st);
+    cudaFreeAsync(fix, st);
+    return rc;
 }
 
 int launch_grad_finish(int64_t n, const unsigned long long *acc, double *grad, cudaStream_t st)
