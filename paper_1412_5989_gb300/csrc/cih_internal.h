@@ -82,6 +82,13 @@ struct DevBasis {
     const int2 *n1p;
     const int16_t *dir;
     int32_t dir_len, NL, DM;
+    // count lists: per proton sub-det p, the directory positions its one-move
+    // candidates' segments start and end at, with multiplicities (position,
+    // coefficient), and the number of candidates whose range holds n itself
+    // per N_n
+    const int64_t *clist_off;  // n_p + 1, or null when the count walks the candidates
+    const int2 *clist;
+    const uint16_t *cself_sfx; // n_p x NL
     const int16_t *self_rel;       // per neutron n: entries of its one-move list below n
     const uint8_t *occ[2];         // per sub-det: its occupied orbitals, ascending (Z_s each)
 };

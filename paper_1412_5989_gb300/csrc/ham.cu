@@ -742,6 +742,42 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     }
 }
 
+// Count pass from the count lists (one warp per row): for row (p, n), 1 for
+// the diagonal + n's forward same-class neighbours inside p's range + the
+// sum over p's list of coefficient x n's directory entry (the pn segment
+// lengths of all of p's one-move candidates) + the candidates whose range
+// holds n itself.  Equal to the walk's count, with no candidate records read.
+__global__ void __launch_bounds__(256) k_count_lists(DevBasis B, int64_t *counts, int64_t r0, int64_t r1)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const DevSpecies &SN = B.sp[1];
+    for (int64_t row = r0 + gw; row < r1; row += nw) {
+        const int p = B.row_p[row];
+        const int nbp = B.nb[p];
+        const int n = nbp + (int)(row - B.rowbase[p]);
+        const int nend = nbp + B.nc[p];
+        const int64_t a0 = SN.fw_off[n], a1 = SN.fw_off[n + 1];
+        int cnt = 0;
+        for (int64_t t0 = a0; t0 < a1; t0 += 32) {          // the forward list is ascending
+            const int64_t t = t0 + lane;
+            const bool in = t < a1 && SN.fw[t] < nend;
+            const unsigned bm = __ballot_sync(0xffffffffu, in);
+            cnt += __popc(bm);
+            if (bm != 0xffffffffu) break;
+        }
+        const int16_t *dirn = B.dir + (int64_t)n * B.dir_len;
+        int acc = 0;
+        for (int64_t q = B.clist_off[p] + lane; q < B.clist_off[p + 1]; q += 32) {
+            const int2 e = B.clist[q];
+            acc += e.y * (int)dirn[e.x];
+        }
+        acc = __reduce_add_sync(0xffffffffu, acc);
+        if (lane == 0) counts[row] = 1 + cnt + acc + B.cself_sfx[(int64_t)p * B.NL + SN.N[n]];
+    }
+}
+
 // Raise a kernel's dynamic shared-memory limit on a device once per size, so
 // that later calls (inside a stream capture, say) only launch.
 cudaError_t raise_smem_limit(const void *kern, int dev, int bytes)
@@ -820,7 +856,17 @@ __global__ void k_fix_to_double(int64_t n, const unsigned long long *acc, double
 
 int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st)
 {
-    return launch_rows<0>(b, nullptr, rowptr, FillArgs{}, GradArgs{}, st);
+    if (!b.dev.clist_off) return launch_rows<0>(b, nullptr, rowptr, FillArgs{}, GradArgs{}, st);
+    if (b.dim == 0) return CIH_OK;
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_lists, 256, 0);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), (b.dim + 7) / 8));
+    count_launches(1);
+    k_count_lists<<<grid, 256, 0, st>>>(b.dev, rowptr, 0, b.dim);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CIH_OK : cuda_fail(e, "count launch");
 }
 
 int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st)

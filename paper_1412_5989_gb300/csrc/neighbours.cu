@@ -597,6 +597,57 @@ __global__ void k_onemove_compact_sort(int64_t n, int cap, const int64_t *off, c
     }
 }
 
+
+// Count lists (see DevBasis): one warp per proton sub-det accumulates the
+// directory coefficients of its one-move candidates (segment end +1, start
+// -1) and the histogram of its candidates' 1 + L_q in shared memory; pass 0
+// writes the number of non-zero coefficients, pass 1 the list (ascending
+// directory position) and the suffix counts #{c : 1 + L_q(c) > N}.
+constexpr int kClistDirCap = 4096;
+template <int PASS>
+__global__ void k_clists(int64_t np, const int64_t *cand_off, const int4 *cand, const uint8_t *cself, int dir_len,
+                         int NL, int64_t *clen, const int64_t *clist_off, int2 *clist, uint16_t *cself_sfx)
+{
+    extern __shared__ int cl_sh[];                 // per warp: int[dir_len] coefficients, int[64] histogram
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int *coef = cl_sh + wid * (dir_len + 64);
+    int *hist = coef + dir_len;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < np; p += nw) {
+        for (int i = lane; i < dir_len; i += 32) coef[i] = 0;
+        for (int i = lane; i < 64; i += 32) hist[i] = 0;
+        __syncwarp();
+        for (int64_t c = cand_off[p] + lane; c < cand_off[p + 1]; c += 32) {
+            const uint8_t sl = cself[c];
+            atomicAdd(&hist[min(sl & 0x7F, 63)], 1);              // > N for every N < NL either way
+            if (!(sl >> 7)) {                                  // one-move: a neutron segment
+                const unsigned y = (unsigned)cand[c].y;
+                atomicAdd(&coef[y >> 16], 1);
+                atomicAdd(&coef[y & 0xFFFF], -1);
+            }
+        }
+        __syncwarp();
+        int64_t out = PASS == 1 ? clist_off[p] : 0;
+        int n = 0;
+        for (int i0 = 0; i0 < dir_len; i0 += 32) {
+            const int i = i0 + lane;
+            const int v = i < dir_len ? coef[i] : 0;
+            const unsigned m = __ballot_sync(0xffffffffu, v != 0);
+            if (PASS == 1 && v != 0) clist[out + n + __popc(m & ((1u << lane) - 1))] = make_int2(i, v);
+            n += __popc(m);
+        }
+        if (PASS == 0 && lane == 0) clen[p] = n;
+        if (PASS == 1)
+            for (int N = lane; N < NL; N += 32) {              // candidates with 1 + L_q > N
+                int s = 0;
+                for (int v = N + 1; v < 64; ++v) s += hist[v];
+                cself_sfx[p * NL + N] = (uint16_t)s;
+            }
+        __syncwarp();
+    }
+}
+
 template <class T>
 int dev_alloc(cih_basis &b, T **p, size_t n)
 {
@@ -1007,6 +1058,38 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
         b.dev.cand = cand;
         b.dev.cand_self = cself;
         b.dev.row_p = row_p;
+        // count lists (the count pass then reads a handful of directory entries per row)
+        b.dev.clist_off = nullptr;
+        b.dev.clist = nullptr;
+        b.dev.cself_sfx = nullptr;
+        if (np > 0 && b.dev.dir_len <= kClistDirCap && b.dev.NL <= 63) {
+            int64_t *clen, *cloff;
+            uint16_t *sfx;
+            if ((rc = dev_alloc(b, &clen, np + 1)) || (rc = dev_alloc(b, &sfx, (size_t)np * b.dev.NL))) return rc;
+            const int wpb = 8;
+            const size_t sh = (size_t)wpb * (b.dev.dir_len + 64) * sizeof(int);
+            if ((e = cudaFuncSetAttribute(k_clists<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh)) != cudaSuccess ||
+                (e = cudaFuncSetAttribute(k_clists<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh)) != cudaSuccess)
+                return cuda_fail(e, "count lists shared memory");
+            const int gcl = (int)std::min<int64_t>((np + wpb - 1) / wpb, 152 * 8);
+            count_launches(1);
+            k_clists<0><<<gcl, 32 * wpb, sh, st>>>(np, coff, cand, cself, b.dev.dir_len, b.dev.NL, clen, nullptr,
+                                                   nullptr, nullptr);
+            if ((rc = exclusive_scan_i64(clen, np, b.scan_scratch, b.scan_scratch_len, st))) return rc;
+            cloff = clen;
+            int64_t *ctot = pin.p + 7;
+            e = cudaMemcpyAsync(ctot, cloff + np, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "count list size");
+            int2 *cl;
+            if ((rc = dev_alloc(b, &cl, std::max<int64_t>(*ctot, 1)))) return rc;
+            count_launches(1);
+            k_clists<1><<<gcl, 32 * wpb, sh, st>>>(np, coff, cand, cself, b.dev.dir_len, b.dev.NL, nullptr, cloff,
+                                                   cl, sfx);
+            b.dev.clist_off = cloff;
+            b.dev.clist = cl;
+            b.dev.cself_sfx = sfx;
+        }
         b.dev.A = b.space.Z + b.space.N;
         b.dev.nZ[0] = b.space.Z;
         b.dev.nZ[1] = b.space.N;
