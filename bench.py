@@ -94,9 +94,14 @@ def fill_traffic(fill_source_sha):
 
 
 def kernel_source_sha():
+    """Hash of the fill kernel's sources with comments and blank space removed,
+    so that only a code change invalidates a recorded capture."""
     h = hashlib.sha256()
     for f in ("ham.cu", "cih_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1412_5989_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1412_5989_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

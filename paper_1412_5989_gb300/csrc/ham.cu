@@ -13,8 +13,11 @@
 //      followed by p's one-move neighbours in later classes; for each q the
 //      neutron partners are n itself (if it lies in q's range) merged with
 //      n's one-move neighbours inside q's range (two-moves of p need n_j = n).
-// A warp owns a row; lanes take candidate proton sub-dets, find their
-// neutron segment by binary search, and a warp scan places the segments.
+// A warp owns a row; lanes take candidate proton sub-dets, read their
+// neutron segment bounds from n's bucket directory, and a warp scan places
+// the segments.  The count pass has a faster form that needs no walk
+// (k_count_lists): per proton sub-det, the directory positions where its
+// segments start and end, summed against n's directory.
 //
 // Matrix elements (bra = row i, ket = column j, R = orbitals common to both):
 // the operator a+_a a+_b a_d a_c with a<b in the bra and c<d in the ket has
