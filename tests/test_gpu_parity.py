@@ -243,3 +243,29 @@ def test_gradient_full_path_mid(cih):
     diag = val0[0].cpu().numpy()[rp0.cpu().numpy()[:-1]]
     e1 = float(np.sum(diag * p * p))
     assert e1 + float(g @ t.astype(np.float64)) == pytest.approx(ev[0][0], rel=1e-6)
+
+
+def test_lanczos_residual_full_size(cih):
+    """4+4 Nmax=6 (925 M stored nonzeros), too large for the oracle's Lanczos:
+    the lowest Ritz pair's residual |H psi - E0 psi| computed independently in
+    torch from the stored half (row part + mirrored part - diagonal)."""
+    sp = (4, 4, 6, 0)
+    B = cih.Basis(*sp)
+    t = synth.tbme_table(B.tbme_len, 0)
+    rowptr, col, val, nnz = cih.build_hamiltonian(B, torch.from_numpy(t).cuda())
+    ev, psi, conv = B.lanczos(rowptr, col, val, nev=1, max_iter=600, tol=1e-9)
+    assert conv
+    x = psi[0]
+    v = val[0].double()
+    rows = torch.repeat_interleave(torch.arange(B.dim, device="cuda"), rowptr[1:] - rowptr[:-1])
+    c = col.long()
+    y = torch.zeros(B.dim, dtype=torch.float64, device="cuda")
+    y.index_add_(0, rows, v * x[c])                                  # upper half
+    y.index_add_(0, c, v * x[rows])                                  # mirrored half
+    diag = rowptr[:-1]
+    y -= v[diag] * x                                                 # the diagonal counted once
+    res = float(torch.linalg.vector_norm(y - ev[0][0] * x))
+    assert abs(float(torch.linalg.vector_norm(x)) - 1.0) < 1e-10
+    assert res <= 1e-6 * abs(ev[0][0]), res
+    del rows, c, v, y, col, val
+    torch.cuda.empty_cache()
