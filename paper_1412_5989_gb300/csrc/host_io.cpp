@@ -14,6 +14,7 @@ int build_host(cih_basis &b, int K, double hw, const float *tbme_h, const double
 {
     const int64_t dim = b.dim, tl = b.layout.total;
     const int n_orb = b.s[0].n_orb + b.s[1].n_orb;
+    Timer tm("build_host");
     std::vector<void *> bufs;
     auto alloc = [&](void **p, size_t bytes) -> bool {
         // the library pool keeps the blocks mapped for the next call
@@ -47,6 +48,7 @@ int build_host(cih_basis &b, int K, double hw, const float *tbme_h, const double
     if (e != cudaSuccess) { rc = cuda_fail(e, "build_host: row pointers"); goto done; }
     nnz = rowptr_h[dim];
     if (nnz_out) *nnz_out = nnz;
+    tm.mark("tables in, count, row pointers out");
     if (nnz > capacity) {
         rc = fail(CIH_ERR_CAPACITY, "build_host: " + std::to_string(nnz) + " stored nonzeros, capacity " +
                                         std::to_string(capacity));
@@ -56,6 +58,7 @@ int build_host(cih_basis &b, int K, double hw, const float *tbme_h, const double
         rc = fail(CIH_ERR_NOMEM, "build_host: device matrix");
         goto done;
     }
+    tm.mark_sync("device matrix allocated", st);
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) { cs = nullptr; rc = cuda_fail(e, "build_host: copy stream"); goto done; }
     {
@@ -84,7 +87,9 @@ int build_host(cih_basis &b, int K, double hw, const float *tbme_h, const double
                                     sizeof(float) * (e1 - e0), cudaMemcpyDeviceToHost, cs);
             }
         }
+        tm.mark_sync("fill chunks done", st);
         e = cudaStreamSynchronize(cs);
+        tm.mark("copies done");
         if (!rc && e != cudaSuccess) rc = cuda_fail(e, "build_host: copies");
         e = cudaGetLastError();
         if (!rc && e != cudaSuccess) rc = cuda_fail(e, "build_host");
