@@ -13,6 +13,7 @@
 #include <cstring>
 
 #include <functional>
+#include <mutex>
 
 #include "cih_internal.h"
 
@@ -711,6 +712,7 @@ struct Lists {
     int *dmax = nullptr;
     int cap1 = 1, grid = 1;
     int64_t *tot = nullptr;                   // pinned: forward and one-move totals
+    int32_t *rn = nullptr;                    // neutron species: pn split row of each orbital (device)
 };
 
 template <int W>
@@ -792,11 +794,10 @@ int lists_phase3(cih_basis &b, int t, SpeciesBuild &S, Lists &L, cudaStream_t st
     }
     if (t == 1) {
         uint32_t *info;
-        int32_t *rn;
-        if ((rc = dev_alloc(b, &info, L.tot[1])) || (rc = upload(b, &rn, b.pn.rn, st))) return rc;
+        if ((rc = dev_alloc(b, &info, L.tot[1]))) return rc;
         if (n > 0) {
             count_launches(1);
-            k_n1_info<W><<<L.grid, 256, 0, st>>>(S, L.cnt_n1, L.n1, rn, info);
+            k_n1_info<W><<<L.grid, 256, 0, st>>>(S, L.cnt_n1, L.n1, L.rn, info);
         }
         b.dev.n1_info = info;
     }
@@ -919,9 +920,66 @@ int basis_tables_upload(cih_basis &b, cudaStream_t st)
     return CIH_OK;
 }
 
+// Page-locked 8-word slots for the totals read back during set-up, kept for the
+// next basis (allocating and freeing pinned memory costs more than the set-up's
+// own synchronisations).
+std::mutex g_slot_mu;
+std::vector<int64_t *> g_slots;
+
 struct PinnedTotals {
     int64_t *p = nullptr;
-    ~PinnedTotals() { if (p) cudaFreeHost(p); }
+    cudaError_t get()
+    {
+        {
+            std::lock_guard<std::mutex> lock(g_slot_mu);
+            if (!g_slots.empty()) {
+                p = g_slots.back();
+                g_slots.pop_back();
+                return cudaSuccess;
+            }
+        }
+        cudaError_t e = cudaMallocHost((void **)&p, 8 * sizeof(int64_t));
+        if (e != cudaSuccess) p = nullptr;
+        return e;
+    }
+    ~PinnedTotals()
+    {
+        if (!p) return;
+        std::lock_guard<std::mutex> lock(g_slot_mu);
+        g_slots.push_back(p);
+    }
+};
+
+// A second stream for the neutron species' list passes, which depend on the
+// proton species' only through the candidate table.  The destructor waits for
+// it, so that no early return leaves its kernels running on buffers the basis
+// then frees.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaError_t create()
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { s = nullptr; return e; }
+        for (auto &x : ev)
+            if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess) { x = nullptr; return e; }
+        return cudaSuccess;
+    }
+    ~SideStream()
+    {
+        if (s) cudaStreamSynchronize(s);
+        for (auto x : ev)
+            if (x) cudaEventDestroy(x);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+// device allocations and frees of a block of calls go to stream s
+struct AllocOn {
+    cih_basis &b;
+    cudaStream_t old;
+    AllocOn(cih_basis &b_, cudaStream_t s) : b(b_), old(b_.stream) { b.stream = s; }
+    ~AllocOn() { b.stream = old; }
 };
 
 }  // namespace
@@ -937,8 +995,8 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
     b.dev.queue = b.dev_status + 1;
     if (cudaMemsetAsync(b.dev_status, 0, 4 * sizeof(int), st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "status");
     PinnedTotals pin;
-    cudaError_t e = cudaMallocHost((void **)&pin.p, 8 * sizeof(int64_t));
-    if (e != cudaSuccess) { pin.p = nullptr; return cuda_fail(e, "pinned totals"); }
+    cudaError_t e = pin.get();
+    if (e != cudaSuccess) return cuda_fail(e, "pinned totals");
     for (int i = 0; i < 8; ++i) pin.p[i] = 0;
     Lists L[2];
     L[0].tot = pin.p;
@@ -948,14 +1006,24 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
         if (64 * W < b.s[t].n_orb || (W != 1 && W != 2 && W != 4))
             return fail(CIH_ERR_UNSUPPORTED, "internal: bit strings of " + std::to_string(W) + " words for " +
                                                  std::to_string(b.s[t].n_orb) + " orbitals");
-    // 1. per species: upload, hash table, staged passes (queued, no synchronisation)
+    // 1. per species, protons on st and neutrons on a second stream: upload,
+    //    hash table, staged passes (queued, no synchronisation).  Uploads from
+    //    pageable memory wait for their own stream only, so neither species'
+    //    uploads wait for the other's kernels.
     SpeciesHost H[2];
     side_by_side([&]() { species_prep(b, 0, H[0]); }, [&]() { species_prep(b, 1, H[1]); });
+    SideStream side;
+    if ((e = side.create()) != cudaSuccess) return cuda_fail(e, "side stream");
+    const cudaStream_t ss[2] = {st, side.s};
+    cudaEventRecord(side.ev[0], st);                   // after the status words are cleared
+    cudaStreamWaitEvent(side.s, side.ev[0], 0);
+    tm.mark("species host arrays");
     for (int t = 0; t < 2; ++t) {
-        if ((rc = species_upload(b, t, H[t], st))) return rc;
-        if (W == 1) rc = lists_phase1<1>(b, t, b.sbuild[t], L[t], st);
-        else if (W == 2) rc = lists_phase1<2>(b, t, b.sbuild[t], L[t], st);
-        else rc = lists_phase1<4>(b, t, b.sbuild[t], L[t], st);
+        AllocOn on(b, ss[t]);
+        if ((rc = species_upload(b, t, H[t], ss[t]))) return rc;
+        if (W == 1) rc = lists_phase1<1>(b, t, b.sbuild[t], L[t], ss[t]);
+        else if (W == 2) rc = lists_phase1<2>(b, t, b.sbuild[t], L[t], ss[t]);
+        else rc = lists_phase1<4>(b, t, b.sbuild[t], L[t], ss[t]);
         if (rc) return rc;
     }
     tm.mark("species queued");
@@ -963,19 +1031,25 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
     if ((rc = host_rest())) return rc;
     tm.mark("host ranges + layout");
     e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(side.s);
     if (e != cudaSuccess) return cuda_fail(e, "neighbour counts");
     tm.mark("staged passes done");
-    // 2. exact-size lists
-    for (int t = 0; t < 2; ++t)
-        if ((rc = lists_phase2(b, t, b.sbuild[t], L[t], st))) return rc;
-    // 3. basis tables, two-move indices, neutron move information
-    if ((rc = basis_tables_upload(b, st))) return rc;
+    // basis tables while both streams are idle (no upload waits for a kernel)
+    if ((rc = basis_tables_upload(b, st)) || (rc = upload(b, &L[1].rn, b.pn.rn, st))) return rc;
+    cudaEventRecord(side.ev[1], st);
+    // 2. exact-size lists, 3. two-move indices and neutron move information,
+    //    again one species per stream; phase 3 reads the basis tables
     for (int t = 0; t < 2; ++t) {
-        if (W == 1) rc = lists_phase3<1>(b, t, b.sbuild[t], L[t], st);
-        else if (W == 2) rc = lists_phase3<2>(b, t, b.sbuild[t], L[t], st);
-        else rc = lists_phase3<4>(b, t, b.sbuild[t], L[t], st);
+        AllocOn on(b, ss[t]);
+        if ((rc = lists_phase2(b, t, b.sbuild[t], L[t], ss[t]))) return rc;
+        if (t == 1) cudaStreamWaitEvent(side.s, side.ev[1], 0);
+        if (W == 1) rc = lists_phase3<1>(b, t, b.sbuild[t], L[t], ss[t]);
+        else if (W == 2) rc = lists_phase3<2>(b, t, b.sbuild[t], L[t], ss[t]);
+        else rc = lists_phase3<4>(b, t, b.sbuild[t], L[t], ss[t]);
         if (rc) return rc;
     }
+    cudaEventRecord(side.ev[2], side.s);               // the rest runs on st, after both species
+    cudaStreamWaitEvent(st, side.ev[2], 0);
     b.scan_scratch_len = scan_scratch_needed(b.dim);
     if ((rc = dev_alloc(b, &b.scan_scratch, b.scan_scratch_len))) return rc;
     {
