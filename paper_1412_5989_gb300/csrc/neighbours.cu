@@ -928,6 +928,7 @@ std::vector<int64_t *> g_slots;
 
 struct PinnedTotals {
     int64_t *p = nullptr;
+    cudaStream_t st = nullptr;                // copies into the slot are queued here
     cudaError_t get()
     {
         {
@@ -945,6 +946,7 @@ struct PinnedTotals {
     ~PinnedTotals()
     {
         if (!p) return;
+        cudaStreamSynchronize(st);            // no copy still in flight into a returned slot
         std::lock_guard<std::mutex> lock(g_slot_mu);
         g_slots.push_back(p);
     }
@@ -995,6 +997,7 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
     b.dev.queue = b.dev_status + 1;
     if (cudaMemsetAsync(b.dev_status, 0, 4 * sizeof(int), st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "status");
     PinnedTotals pin;
+    pin.st = st;
     cudaError_t e = pin.get();
     if (e != cudaSuccess) return cuda_fail(e, "pinned totals");
     for (int i = 0; i < 8; ++i) pin.p[i] = 0;
@@ -1048,12 +1051,12 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
         else rc = lists_phase3<4>(b, t, b.sbuild[t], L[t], ss[t]);
         if (rc) return rc;
     }
-    cudaEventRecord(side.ev[2], side.s);               // the rest runs on st, after both species
-    cudaStreamWaitEvent(st, side.ev[2], 0);
     b.scan_scratch_len = scan_scratch_needed(b.dim);
     if ((rc = dev_alloc(b, &b.scan_scratch, b.scan_scratch_len))) return rc;
     {
-        // neutron one-move lists: packed entries and bucket directory
+        // neutron one-move lists: packed entries and bucket directory, and the
+        // neutron occupied lists, on the second stream; the proton occupied
+        // lists, candidate table and count lists (which read none of these) on st
         const Species &Q = b.s[1];
         int dm = 0;
         for (int x = 0; x < Q.n_orb; ++x)
@@ -1064,32 +1067,33 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
         const int64_t nn = Q.n_sd;
         const int64_t tot = L[1].tot[1];
         int2 *n1p;
-        int16_t *dir;
-        if ((rc = dev_alloc(b, &n1p, tot)) || (rc = dev_alloc(b, &dir, (size_t)nn * dir_len))) return rc;
-        if (nn > 0) {
-            count_launches(2);
-            k_n1_pack<<<(int)std::min<int64_t>((tot + 255) / 256 + 1, 65535), 256, 0, st>>>(
-                nn, b.dev.sp[1].n1_off, b.dev.sp[1].n1, b.dev.n1_info, n1p);
-            k_dir<<<grid_for(nn), 256, 0, st>>>(b.sbuild[1], b.dev.sp[1].n1_off, b.dev.sp[1].n1, NL, dm, dir_len, dir);
-        }
-        int16_t *srel;
+        int16_t *dir, *srel;
         uint8_t *occp, *occn;
-        if ((rc = dev_alloc(b, &srel, nn)) || (rc = dev_alloc(b, &occp, (size_t)b.s[0].n_sd * std::max(b.s[0].Z, 1))) ||
-            (rc = dev_alloc(b, &occn, (size_t)nn * std::max(Q.Z, 1))))
-            return rc;
         const int g0 = (int)std::min<int64_t>((b.s[0].n_sd + 255) / 256 + 1, 65535);
         const int g1 = (int)std::min<int64_t>((nn + 255) / 256 + 1, 65535);
-        count_launches(2);
-        if (W == 1) {
-            k_occ<1><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
-            k_occ<1><<<g1, 256, 0, st>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
-        } else if (W == 2) {
-            k_occ<2><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
-            k_occ<2><<<g1, 256, 0, st>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
-        } else {
-            k_occ<4><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
-            k_occ<4><<<g1, 256, 0, st>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
+        {
+            AllocOn on(b, side.s);
+            if ((rc = dev_alloc(b, &n1p, tot)) || (rc = dev_alloc(b, &dir, (size_t)nn * dir_len)) ||
+                (rc = dev_alloc(b, &srel, nn)) || (rc = dev_alloc(b, &occn, (size_t)nn * std::max(Q.Z, 1))))
+                return rc;
+            if (nn > 0) {
+                count_launches(2);
+                k_n1_pack<<<(int)std::min<int64_t>((tot + 255) / 256 + 1, 65535), 256, 0, side.s>>>(
+                    nn, b.dev.sp[1].n1_off, b.dev.sp[1].n1, b.dev.n1_info, n1p);
+                k_dir<<<grid_for(nn), 256, 0, side.s>>>(b.sbuild[1], b.dev.sp[1].n1_off, b.dev.sp[1].n1, NL, dm,
+                                                        dir_len, dir);
+            }
+            count_launches(1);
+            if (W == 1) k_occ<1><<<g1, 256, 0, side.s>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
+            else if (W == 2) k_occ<2><<<g1, 256, 0, side.s>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
+            else k_occ<4><<<g1, 256, 0, side.s>>>(b.sbuild[1], Q.Z, b.dev.sp[1].n1_off, b.dev.sp[1].n1, occn, srel);
         }
+        cudaEventRecord(side.ev[2], side.s);           // the neutron half is complete here
+        if ((rc = dev_alloc(b, &occp, (size_t)b.s[0].n_sd * std::max(b.s[0].Z, 1)))) return rc;
+        count_launches(1);
+        if (W == 1) k_occ<1><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
+        else if (W == 2) k_occ<2><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
+        else k_occ<4><<<g0, 256, 0, st>>>(b.sbuild[0], b.s[0].Z, nullptr, nullptr, occp, nullptr);
         b.dev.self_rel = srel;
         b.dev.occ[0] = occp;
         b.dev.occ[1] = occn;
@@ -1168,6 +1172,7 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
         b.dev.nZ[0] = b.space.Z;
         b.dev.nZ[1] = b.space.N;
     }
+    cudaStreamWaitEvent(st, side.ev[2], 0);            // join: later work on st sees both species
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "basis upload");
     b.dev.max_cand = (int32_t)L[0].tot[2];
