@@ -53,10 +53,11 @@ void make_orbitals(Species &s, int top_shell)
 }
 
 // Sub-determinants of one species in (2M, N mod 2, N, bits) order, in two
-// parallel passes over the highest occupied orbital `top`: pass 1 counts the
-// subsets of each (top, bucket) with bucket = (2M, N mod 2, N); a prefix sum in
-// (bucket, top) order gives each pair its slot; pass 2 writes every subset to
-// its slot.  Inside one (top, bucket) the recursion visits subsets in
+// passes over the highest occupied orbital `top`: pass 1 counts the subsets of
+// each (top, bucket) with bucket = (2M, N mod 2, N), by a counting recursion
+// over the orbitals rather than by enumeration; a prefix sum in (bucket, top)
+// order gives each pair its slot; pass 2, in parallel over the tops,
+// enumerates and writes every subset to its slot.  Inside one (top, bucket) the recursion visits subsets in
 // ascending bit-string order (colexicographic: highest element first), and
 // slots of the same bucket are ordered by top, so each bucket comes out
 // sorted by the bit string read as an unsigned integer.
@@ -143,15 +144,42 @@ void count_subdets(const Species &s, SubdetCount &C)
         if (s.oN[a] + E.minsum[s.Z - 1] <= budget) C.tops.push_back(a);
     const int ntop = (int)C.tops.size();
     C.nk = E.nkeys();
-    C.cnt.assign((size_t)ntop * C.nk, 0);          // one row per top: no shared counters
-    parallel_tops(ntop, [&](int t) {
-        uint64_t w[kMaxWords] = {0, 0, 0, 0};
-        const int a = C.tops[t];
-        w[a >> 6] |= 1ull << (a & 63);
-        int64_t *c = &C.cnt[(size_t)t * C.nk];
-        auto f = [&](const uint64_t *, int N, int M) { c[E.key(N, M)]++; };
-        E.rec(w, s.Z - 1, a, budget - s.oN[a], s.oN[a], s.om2[a], f);
-    });
+    C.cnt.assign((size_t)ntop * C.nk, 0);          // one row per top
+    // The counts need no enumeration: with the orbitals taken in index order,
+    // T[c][N][2M] holds the number of c-subsets of the orbitals below the
+    // current one with quanta N and projection 2M (a generating-function
+    // recursion).  Top a's row is T[Z-1] shifted by a's own (N, 2M); then a is
+    // added to every subset of fewer than Z-1 orbitals.  Since orbitals come in
+    // ascending N, a c-subset below a still takes Z-c orbitals of at least N_a,
+    // which bounds the useful N.
+    const int Z = s.Z, NB = budget + 1, MS = 2 * E.Mabs + 1;
+    std::vector<int64_t> T((size_t)Z * NB * MS, 0);
+    auto row = [&](int c, int N) { return &T[((size_t)c * NB + N) * MS + E.Mabs]; };   // index by 2M
+    row(0, 0)[0] = 1;
+    int mreach = 0;                                // largest |2m| among the orbitals so far
+    for (int a = 0, t = 0; a < s.n_orb && t < ntop; ++a) {
+        const int Na = s.oN[a], ma = s.om2[a];
+        mreach = std::max(mreach, std::abs(ma));
+        if (a == C.tops[t]) {
+            int64_t *cnt = &C.cnt[(size_t)t * C.nk];
+            const int Mr = std::min(E.Mabs, (Z - 1) * mreach);
+            for (int N = 0; N + Na <= budget; ++N) {
+                const int64_t *r = row(Z - 1, N);
+                for (int M = -Mr; M <= Mr; ++M)
+                    if (r[M]) cnt[E.key(N + Na, M + ma)] += r[M];
+            }
+            ++t;
+        }
+        for (int c = std::min(Z - 2, a); c >= 0; --c) {
+            const int Mr = std::min(E.Mabs, c * mreach);
+            for (int N = 0; N + (Z - c) * Na <= budget; ++N) {
+                const int64_t *r = row(c, N);
+                int64_t *o = row(c + 1, N + Na) + ma;
+                for (int M = -Mr; M <= Mr; ++M)
+                    if (r[M]) o[M] += r[M];
+            }
+        }
+    }
     C.total.assign(C.nk, 0);
     for (int t = 0; t < ntop; ++t)
         for (int64_t k = 0; k < C.nk; ++k) C.total[k] += C.cnt[(size_t)t * C.nk + k];
