@@ -745,39 +745,60 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     }
 }
 
-// Count pass from the count lists (one warp per row): for row (p, n), 1 for
-// the diagonal + n's forward same-class neighbours inside p's range + the
-// sum over p's list of coefficient x n's directory entry (the pn segment
-// lengths of all of p's one-move candidates) + the candidates whose range
-// holds n itself.  Equal to the walk's count, with no candidate records read.
+// Count pass from the count lists: for row (p, n), 1 for the diagonal + n's
+// forward same-class neighbours inside p's range + the sum over p's list of
+// coefficient x n's directory entry (the pn segment lengths of all of p's
+// one-move candidates) + the candidates whose range holds n itself.  Equal to
+// the walk's count, with no candidate records read.  Each row is a chain of
+// dependent loads (row -> p -> n -> lists), so a warp takes 32 / G rows at a
+// time, G lanes each, to keep that many chains in flight; every warp-wide
+// intrinsic is reached by all 32 lanes.
+template <int G>
 __global__ void __launch_bounds__(256) k_count_lists(DevBasis B, int64_t *counts, int64_t r0, int64_t r1)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31, g = lane / G, li = lane % G;
+    const unsigned full = 0xffffffffu, gbits = G == 32 ? full : (1u << G) - 1u;
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const DevSpecies &SN = B.sp[1];
-    for (int64_t row = r0 + gw; row < r1; row += nw) {
-        const int p = B.row_p[row];
-        const int nbp = B.nb[p];
-        const int n = nbp + (int)(row - B.rowbase[p]);
-        const int nend = nbp + B.nc[p];
-        const int64_t a0 = SN.fw_off[n], a1 = SN.fw_off[n + 1];
+    for (int64_t base = r0 + gw * R; base < r1; base += nw * R) {      // uniform over the warp
+        const int64_t row = base + g;
+        const bool live = row < r1;
+        int p = 0, n = 0, nend = 0;
+        int64_t a0 = 0, a1 = 0, q0 = 0, q1 = 0;
+        if (live) {
+            p = B.row_p[row];
+            const int nbp = B.nb[p];
+            n = nbp + (int)(row - B.rowbase[p]);
+            nend = nbp + B.nc[p];
+            a0 = SN.fw_off[n];
+            a1 = SN.fw_off[n + 1];
+            q0 = B.clist_off[p];
+            q1 = B.clist_off[p + 1];
+        }
+        // forward list, ascending: its entries below nend, G at a time
         int cnt = 0;
-        for (int64_t t0 = a0; t0 < a1; t0 += 32) {          // the forward list is ascending
-            const int64_t t = t0 + lane;
-            const bool in = t < a1 && SN.fw[t] < nend;
-            const unsigned bm = __ballot_sync(0xffffffffu, in);
-            cnt += __popc(bm);
-            if (bm != 0xffffffffu) break;
+        bool more = live;
+        for (int64_t t0 = a0; __any_sync(full, more); t0 += G) {
+            const int64_t t = t0 + li;
+            const bool in = more && t < a1 && SN.fw[t] < nend;
+            const unsigned bm = (__ballot_sync(full, in) >> (g * G)) & gbits;
+            if (more) {
+                cnt += __popc(bm);
+                more = bm == gbits;                    // the same in every lane of the group
+            }
         }
         const int16_t *dirn = B.dir + (int64_t)n * B.dir_len;
         int acc = 0;
-        for (int64_t q = B.clist_off[p] + lane; q < B.clist_off[p + 1]; q += 32) {
+#pragma unroll 4
+        for (int64_t q = q0 + li; q < q1; q += G) {
             const int2 e = B.clist[q];
             acc += e.y * (int)dirn[e.x];
         }
-        acc = __reduce_add_sync(0xffffffffu, acc);
-        if (lane == 0) counts[row] = 1 + cnt + acc + B.cself_sfx[(int64_t)p * B.NL + SN.N[n]];
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(full, acc, o);
+        if (live && li == 0) counts[row] = 1 + cnt + acc + B.cself_sfx[(int64_t)p * B.NL + SN.N[n]];
     }
 }
 
@@ -864,10 +885,13 @@ int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st)
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_lists, 256, 0);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), (b.dim + 7) / 8));
+    constexpr int G = 8;                                     // lanes per row
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_lists<G>, 256, 0);
+    const int64_t rows_per_block = 8 * (32 / G);
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sms * std::max(per_sm, 1), (b.dim + rows_per_block - 1) / rows_per_block));
     count_launches(1);
-    k_count_lists<<<grid, 256, 0, st>>>(b.dev, rowptr, 0, b.dim);
+    k_count_lists<G><<<grid, 256, 0, st>>>(b.dev, rowptr, 0, b.dim);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? CIH_OK : cuda_fail(e, "count launch");
 }
