@@ -939,7 +939,7 @@ struct PinnedTotals {
                 return cudaSuccess;
             }
         }
-        cudaError_t e = cudaMallocHost((void **)&p, 8 * sizeof(int64_t));
+        cudaError_t e = cudaHostAlloc((void **)&p, 8 * sizeof(int64_t), cudaHostAllocPortable);   // any device
         if (e != cudaSuccess) p = nullptr;
         return e;
     }
