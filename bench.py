@@ -78,6 +78,28 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def write_only_gbs(dev, st, nbytes=4 << 30, reps=5):
+    """Write-only streaming bandwidth of this GPU, the second roofline
+    denominator next to the measured copy: a float32 fill of a buffer larger
+    than L2 (16-byte stores), CUDA events on the launching stream, best of
+    `reps`.  Measurement only; no part of the construction path."""
+    import torch
+    buf = torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
+    buf.fill_(0.0)
+    best = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        buf.fill_(1.0)
+        b.record(st)
+        torch.cuda.synchronize()
+        best = max(best, buf.numel() * 4 / (a.elapsed_time(b) * 1e-3) / 1e9)
+    del buf
+    torch.cuda.empty_cache()
+    return best
+
+
 def fill_traffic(fill_source_sha):
     """DRAM bytes per fill launch from the committed ncu summary, if it was taken
     on the current fill kernel (same source hash); else None."""
@@ -436,12 +458,15 @@ def run_ours(args, rank, world, local_rank):
     extra = {} if (args.no_extra or K > 1) else side_measurements(args, dev, st, flush, peak, cih, synth, sp, rowptr, col, val, nnz)
     fill_ms = statistics.median(t_fill)
     achieved = nnz * bytes_per_nnz / (fill_ms * 1e-3) / 1e9
+    wpeak = write_only_gbs(dev, st)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "kernel": "k_rows<W,1,K1> (fill)" if K == 1 else f"k_rows<W,1> (batched fill, K={K})",
                 "algorithmic_bytes_per_launch": nnz * bytes_per_nnz,
-                "traffic": fill_traffic(kernel_source_sha()) if (args.workload == "4p4n_nmax6" and K == 1) else None}
+                "traffic": fill_traffic(kernel_source_sha()) if (args.workload == "4p4n_nmax6" and K == 1) else None,
+                "write_only_peak": wpeak, "frac_of_write_only": achieved / wpeak,
+                "write_only_source": "float32 fill of a 4 GiB buffer on this GPU, best of 5, CUDA events"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and K == 1:
