@@ -199,6 +199,20 @@ def oracle_rate(w, rows_n, seed=1):
     return float(cnt.sum()) / dt, int(cnt.sum()), dt, threads, len(rows)
 
 
+def oracle_rate_one_thread(workload, rows_n, seed=2, timeout=900):
+    """The same oracle sample on one host thread: a child process started with
+    OMP_NUM_THREADS=1 (the OpenMP runtime reads it once per process).  Returns
+    (nnz/s, nnz in sample, seconds, threads)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "r, n, dt, th, rows = bench.oracle_rate(bench.WORKLOADS[%r], %d, seed=%d); "
+            "print(json.dumps([r, n, dt, th]))") % (ROOT, workload, rows_n, seed)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=timeout, check=True)
+    r, n, dt, th = json.loads(out.stdout.strip().splitlines()[-1])
+    return float(r), int(n), float(dt), int(th)
+
+
 def max_over_ranks(x, world, device=None):
     """The largest value of x over the ranks (replicas report the slowest)."""
     if world <= 1:
@@ -474,6 +488,13 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": r, "unit": "nnz/s", "cores": threads, "kind": "oracle",
                "sample": f"{rows} random rows of {args.workload} ({n} nonzeros, {dt:.1f} s): count + fill by "
                          f"the oracle's plain row walk, OpenMP over rows"}
+        rows1 = max(50, args.cpu_rows // 25)
+        try:
+            r1, n1, dt1, th1 = oracle_rate_one_thread(args.workload, rows1)
+            cpu["one_thread"] = {"value": r1, "unit": "nnz/s", "cores": th1,
+                                 "sample": f"{rows1} other random rows ({n1} nonzeros, {dt1:.1f} s), same walk"}
+        except (subprocess.SubprocessError, OSError, ValueError) as e:
+            cpu["one_thread"] = {"value": None, "error": str(e)[:200]}
 
     if rank == 0:
         print(json.dumps({

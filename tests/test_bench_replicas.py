@@ -83,3 +83,12 @@ def test_reference_arm_rank_zero_prints_one_line():
     assert d["impl"] == "reference" and d["unit"] == "nnz/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_oracle_one_thread_child_process():
+    """The single-thread oracle timing runs in a child with OMP_NUM_THREADS=1
+    and reports the same kind of sample as the all-core run."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r, n, dt, th = bench.oracle_rate_one_thread("3p3n_nmax2", 200)
+    assert th == 1 and n > 0 and dt > 0 and r == pytest.approx(n / dt)
