@@ -493,7 +493,7 @@ def run_ours(args, rank, world, local_rank):
             r1, n1, dt1, th1 = oracle_rate_one_thread(args.workload, rows1)
             cpu["one_thread"] = {"value": r1, "unit": "nnz/s", "cores": th1,
                                  "sample": f"{rows1} other random rows ({n1} nonzeros, {dt1:.1f} s), same walk"}
-        except (subprocess.SubprocessError, OSError, ValueError) as e:
+        except (subprocess.SubprocessError, OSError, ValueError, IndexError) as e:
             cpu["one_thread"] = {"value": None, "error": str(e)[:200]}
 
     if rank == 0:
