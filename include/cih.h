@@ -81,7 +81,9 @@ typedef struct cih_basis *cih_basis_h;
  * the index tables that define the basis come before the matrix): orbitals,
  * sub-determinants of both species, partner ranges, row offsets, the
  * two-body table layout, and the neighbour lists the kernels walk.  Work is
- * ordered on `stream`; the call returns after the stream has finished it.
+ * ordered after `stream`'s earlier work; the neutron half of the list passes
+ * runs on a second, library-created stream that joins `stream` before the
+ * call returns, and the call returns after both have finished.
  * *out receives a new handle (release with cih_basis_destroy).
  * Errors: CIH_ERR_ARG (NULL, Z or N < 0, Nmax < 0), CIH_ERR_UNSUPPORTED
  * (more than 256 orbitals per species, a dimension above 2^31-1, a
