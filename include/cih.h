@@ -44,7 +44,10 @@
  * layout, scan scratch).  Every call is ordered on the given CUDA stream
  * (a cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
  * that return a host value (nnz_out, evals_host) synchronise that stream.
- * A handle must not be used by two host threads at once.
+ * A handle must not be used by two host threads at once.  The library keeps
+ * per-device state for the life of the process (its memory pool, the device
+ * address of cih_rowptr_scan_static's array); resetting a device after the
+ * library has used it is not supported.
  *
  * Errors: every call returns 0 or a negative CIH_ERR_* code; no C++ exception
  * crosses the ABI.  cih_strerror() names a code; cih_last_error_detail()
@@ -135,8 +138,13 @@ int cih_ham_count(cih_basis_h h, int64_t *rowptr_dev, int64_t *nnz_out, void *st
  *   tbme_dev: K x tbme_len float (device), set-major, layout above;
  *   e_sp_dev: NULL for e_a = hbar_omega (N_a + 3/2), else (n_orb_p +
  *             n_orb_n) double one-body energies (device, combined index).
- * Values are FP64 sums of FP32 table entries, in a fixed order (one-body
- * terms by orbital, then two-body terms by spectator / pair), rounded once.
+ * Values: single-term elements (two-particle moves) are the table entry
+ * times +-1, exactly.  Multi-term elements (the diagonal, one-particle moves)
+ * are sums of FP32 terms (one-body energies, table entries) carried as
+ * double-float pairs (hi + lo, about 48 significant bits), rounded once to
+ * FP32.  For the few dozen terms of one element this is the exact sum in all
+ * but pathological cancellations, so the stored value agrees with the FP64
+ * sum rounded to FP32 within 1e-5 (|value| + 1) (in practice bit for bit).
  * Errors: CIH_ERR_ARG (K < 1, NULL arrays), CIH_ERR_CUDA. */
 int cih_ham_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,
                  const float *tbme_dev, const double *e_sp_dev,
@@ -192,6 +200,14 @@ int cih_tbme_interleave(int32_t K, int64_t tbme_len, const float *tbme_dev, floa
  * Errors: CIH_ERR_ARG. */
 int cih_set_launch(cih_basis_h h, int32_t warps_per_cta, int32_t ctas_per_sm);
 
+/* Which form of the count pass (Sec. 4.1's first pass) cih_ham_count runs for
+ * this handle: walk = 0 (default) sums each row's segment lengths from the
+ * per-proton count lists where the basis has them (bucket directories of at
+ * most 4096 entries and at most 63 oscillator levels) and walks the
+ * candidates otherwise; walk = 1 always walks the candidates, the same walk
+ * the fill makes.  Both give the same row pointers.  Errors: CIH_ERR_ARG. */
+int cih_set_count_mode(cih_basis_h h, int32_t walk);
+
 /* Autotuner: times the fill (cih_ham_fill; cih_ham_fill_interleaved when
  * interleaved == 1; cih_ham_fill_batched when interleaved == 2; same
  * arguments) for every launch shape -- warps per CTA in
@@ -208,7 +224,7 @@ int cih_autotune_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, doubl
  * structure (the output of one cih_ham_fill call): FP32 half-stored values,
  * FP64 vectors and matrix-vector accumulation, FP64 full reorthogonalisation
  * (classical Gram-Schmidt twice per step), FP64 tridiagonal eigenvalues by
- * bisection on the host.  All K Krylov sequences advance together; a set whose
+ * implicit QR on the host.  All K Krylov sequences advance together; a set whose
  * nev residual bounds beta_m |z_m| meet tol * max(1, |theta|) stops there.
  *   val_dev: K x nnz float (set-major); 1 <= K <= 256; nev <= 64: eigenvalues
  *   wanted; max_iter <= 2048: Lanczos steps; tol: relative residual bound on the nev Ritz
@@ -241,9 +257,10 @@ int cih_lanczos_lowest_em(cih_basis_h h, const int64_t *rowptr_dev, const int32_
  * arithmetic throughout, so the sum is deterministic: psi is held as
  * psi_i * 2^61 (int64), each product psi_i psi_j as the high word of the
  * 128-bit product (2^-58 units), and g accumulates in 2^-56 units.
- *   psi_dev: K x dim double (device), |psi_i| < 4 (a normalised vector
- *   qualifies; a larger entry sets the device status that cih_check reports
- *   and counts as 0); grad_dev: K x tbme_len double (device, caller-owned,
+ *   psi_dev: K x dim double (device), each set normalised: |psi_i| < 4
+ *   and sum_i psi_i^2 <= 1 + 1e-6 (a larger entry counts as 0; either
+ *   violation sets the device status that cih_check reports, since the
+ *   fixed-point sums hold |g_t| < 128 and |g_t| <= 2 ||psi||^2); grad_dev: K x tbme_len double (device, caller-owned,
  *   overwritten).
  * Scratch: K x tbme_len int64 and K x dim int64, library-allocated for the
  * call.  Errors: CIH_ERR_ARG, CIH_ERR_NOMEM, CIH_ERR_CUDA. */
@@ -313,15 +330,18 @@ int cih_tridiag_eigen(int32_t n, const double *diag, const double *offdiag, doub
  * Writes the exclusive prefix sum of counts_dev[0..n) into rowptr_dev[0..n]
  * (rowptr[0] = 0, rowptr[n] = total), the same result as the scan inside
  * cih_ham_count.  Both arrays are device memory owned by the caller;
- * counts_dev may equal rowptr_dev (scan in place).  Stream-ordered on
- * `stream`; does not synchronise.
+ * counts_dev may equal rowptr_dev (scan in place), but the two must not
+ * otherwise overlap (CIH_ERR_ARG).  Stream-ordered on `stream`; does not
+ * synchronise.
  *
  * Scratch: the block sums live in a fixed 128 KiB array inside the library
  * (16,384 int64), which every GPU that loads the library holds until the
  * process exits.  Hence n is limited to 67,108,864 (16,384 tiles of 4,096
  * rows); larger n returns CIH_ERR_CAPACITY.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * current; make that first call before any stream capture.  The address is
+ * kept for the life of the process: resetting the device (cudaDeviceReset or
+ * a primary-context reset) after that first call is not supported.  All calls share
  * the array: calls whose work can overlap on the GPU (other streams, other
  * host threads) race and must be serialised by the caller.
  * Errors: CIH_ERR_ARG, CIH_ERR_CAPACITY, CIH_ERR_CUDA. */

@@ -50,6 +50,7 @@ _SIGS = {
     "cih_tbme_interleave": [C.c_int32, C.c_int64, _P, _P, _P],
     "cih_ham_build_host": [_P, C.c_int32, C.c_double, _P, _P, _P, _P, _P, C.c_int64, _i64p, _P],
     "cih_set_launch": [_P, C.c_int32, C.c_int32],
+    "cih_set_count_mode": [_P, C.c_int32],
     "cih_autotune_fill": [_P, _P, C.c_int32, C.c_double, _P, C.c_int32, _P, _P, _P, _P,
                           _i32p, _i32p, C.POINTER(C.c_float)],
     "cih_check": [_P, _P],
@@ -118,7 +119,12 @@ def rowptr_scan_static(counts, rowptr=None, stream=None):
         raise ValueError("counts must be a contiguous int64 CUDA tensor")
     if rowptr is None:
         rowptr = torch.empty(n + 1, dtype=torch.int64, device=counts.device)
-    _ok(lib.cih_rowptr_scan_static(_ptr(counts), n, _ptr(rowptr), _stream(stream)), "rowptr_scan_static")
+    elif (rowptr.dtype != torch.int64 or not rowptr.is_cuda or not rowptr.is_contiguous()
+          or rowptr.numel() < n + 1 or rowptr.device != counts.device):
+        raise ValueError("rowptr must be a contiguous int64 CUDA tensor of at least n + 1 entries "
+                         "on the device of counts")
+    with torch.cuda.device(counts.device):
+        _ok(lib.cih_rowptr_scan_static(_ptr(counts), n, _ptr(rowptr), _stream(stream)), "rowptr_scan_static")
     return rowptr
 
 
@@ -302,6 +308,11 @@ class Basis:
     def set_launch(self, warps_per_cta: int, ctas_per_sm: int = 0):
         """Launch shape of this basis' row kernels."""
         _ok(lib.cih_set_launch(self._h, warps_per_cta, ctas_per_sm), "set_launch")
+
+    def set_count_mode(self, walk: bool):
+        """Count pass of this basis: walk the candidates (True) or sum the
+        count lists where the basis has them (False, the default)."""
+        _ok(lib.cih_set_count_mode(self._h, int(bool(walk))), "set_count_mode")
 
     def autotune_fill(self, rowptr, nnz: int, tbme, hbar_omega: float = 20.0, e_sp=None, *, K: int | None = None,
                       interleaved: bool = False, batched: bool = False, stream=None, col=None, val=None):

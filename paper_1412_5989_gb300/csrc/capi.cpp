@@ -300,6 +300,14 @@ int cih_set_launch(cih_basis_h h, int32_t warps_per_cta, int32_t ctas_per_sm)
     return CIH_OK;
 }
 
+int cih_set_count_mode(cih_basis_h h, int32_t walk)
+{
+    if (!h) return fail(CIH_ERR_ARG, "NULL handle");
+    if (walk != 0 && walk != 1) return fail(CIH_ERR_ARG, "count mode must be 0 (count lists) or 1 (walk)");
+    h->count_walk = walk;
+    return CIH_OK;
+}
+
 int cih_autotune_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega, const float *tbme_dev,
                       int32_t interleaved, const double *e_sp_dev, int32_t *col_dev, float *val_dev, void *stream,
                       int32_t *best_warps, int32_t *best_ctas, float *best_ms)
@@ -356,7 +364,8 @@ int cih_check(cih_basis_h h, void *stream)
     if (status)
         return fail(CIH_ERR_DEVICE, std::string("device status bits ") + std::to_string(status) +
                                         " (1: pair outside the table layout, 2: write beyond the row, "
-                                        "4: two-move index, 8: deferred queue, 32: adjoint vector entry of magnitude 4 or more); first: " + std::to_string(st4[2]) + " " +
+                                        "4: two-move index, 8: deferred queue, 32: adjoint vector not normalised (an entry of magnitude 4 "
+                                        "or more, or a squared norm above 1 + 1e-6)); first: " + std::to_string(st4[2]) + " " +
                                         std::to_string(st4[3]));
     return CIH_OK;
 }

@@ -179,6 +179,7 @@ struct cih_basis {
     cudaStream_t stream = nullptr;            // stream of the build
     int launch_warps = 16;                    // row kernels: warps per CTA (8 or 16)
     int launch_ctas = 0;                      // row kernels: CTAs per SM (0 = as many as fit)
+    int count_walk = 0;                       // count pass: 1 = walk the candidates even with count lists
 };
 
 namespace cih {
@@ -258,8 +259,9 @@ int64_t scan_scratch_needed(int64_t n);
 
 // symmetric tridiagonal eigenproblem, ascending, Z row-major n x n (tridiag.cpp)
 void tridiag_qr(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &Z);
-// r-th smallest eigenvalue by bisection, and its normalised eigenvector by inverse iteration
-double tridiag_eigenvalue(int n, const double *d, const double *e, int r);
+// the same eigenvalues with only the last component of each eigenvector
+void tridiag_qr_last(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &zlast);
+// normalised eigenvector for an eigenvalue by inverse iteration
 void tridiag_eigenvector(int n, const double *d, const double *e, double theta, double *z);
 
 // Lanczos (lanczos.cu)

@@ -31,6 +31,7 @@
 #include <mutex>
 
 #include "cih_internal.h"
+#include "ham_common.cuh"
 
 namespace cih {
 namespace {
@@ -67,38 +68,6 @@ __device__ __forceinline__ long long psi_prod(const long long *psi, int64_t i, i
     return __mul64hi(psi[i], psi[j]);
 }
 
-// Table index of V(ab, cd) for combined orbitals in any order; false if the
-// pairs are not one table entry (a bug in the walk: flagged by the caller).
-// The group sizes and offsets come from shared memory (lg: size and offset
-// per group, int2) when the layout has at most kLayoutCap groups.
-constexpr int kLayoutCap = 512;
-constexpr int kOrbCap = 512;      // combined orbitals (two species of at most 256)
-__device__ __forceinline__ bool tbme_at(const DevBasis &B, const int2 *lg, int a, int b, int c, int d, int64_t &idx,
-                                        int &sign)
-{
-    if ((unsigned)a >= (unsigned)B.ntot || (unsigned)b >= (unsigned)B.ntot ||
-        (unsigned)c >= (unsigned)B.ntot || (unsigned)d >= (unsigned)B.ntot)
-        return false;
-    int32_t e1 = B.pid[a * B.ntot + b], e2 = B.pid[c * B.ntot + d];
-    if (e1 < 0 || e2 < 0) return false;
-    int g = (e1 >> 16) & 0xFFF;
-    if (g != ((e2 >> 16) & 0xFFF)) return false;
-    sign = (((e1 ^ e2) >> 30) & 1) ? -1 : 1;
-    int u = e1 & 0xFFFF, v = e2 & 0xFFFF;
-    if (u > v) { const int t = u; u = v; v = t; }
-    int64_t n, off;
-    if (B.ngroups <= kLayoutCap) {
-        const int2 q = lg[g];
-        n = q.x;
-        off = q.y;
-    } else {
-        n = B.gsize[g];
-        off = B.goff[g];
-    }
-    idx = off + (int64_t)u * n - (int64_t)u * (u - 1) / 2 + (v - u);
-    return true;
-}
-
 // ---------------------------------------------------------------- row kernel
 //
 // Warps walk rows independently (grid-stride); a CTA only shares the pn
@@ -118,7 +87,6 @@ __device__ __forceinline__ bool tbme_at(const DevBasis &B, const int2 *lg, int a
 //   deferred  - one-move elements, lanes over (element, spectator) pairs and
 //               a segmented FP64 reduction.
 
-constexpr int kGroupCap = 128;
 constexpr int kLaneSets = 16;     // from this many sets on, multi-term sums run with lanes over sets
 constexpr int kSlowCap = 64;
 constexpr int kMaxA = 64;
@@ -157,25 +125,6 @@ __device__ __forceinline__ double warp_sum(double v, int width)
     return v;
 }
 
-// A sum of FP32 terms carried as the unevaluated pair hi + lo of floats
-// (Dekker's two-sum), about 48 significant bits: exact for the value sums here
-// (at most a few dozen FP32 terms within 24 binary orders of magnitude), and
-// single-precision arithmetic runs at full rate where the GPU's FP64 units are
-// few.  The value stored is hi + lo rounded once to FP32.
-struct DF {
-    float hi, lo;
-};
-__device__ __forceinline__ DF df_add(DF a, DF b)
-{
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    const float e = (a.hi - (s - bb)) + (b.hi - bb);
-    const float lo = (e + a.lo) + b.lo;
-    const float hi = s + lo;
-    return DF{hi, lo - (hi - s)};
-}
-__device__ __forceinline__ DF df_of(float x) { return DF{x, 0.f}; }
-__device__ __forceinline__ float df_round(DF v) { return v.hi + v.lo; }
 __device__ __forceinline__ DF warp_sum(DF v, int width)
 {
     for (int d = width >> 1; d > 0; d >>= 1) {
@@ -183,19 +132,6 @@ __device__ __forceinline__ DF warp_sum(DF v, int width)
         v = df_add(v, o);
     }
     return v;
-}
-
-// table index of a pn element from the candidate (uv, mv) and neutron move (ni)
-__device__ __forceinline__ int pn_index_at(const int16_t *S, const int32_t *gs, const int32_t *go, uint32_t uv,
-                                           uint32_t mv, uint32_t ni, int &sign)
-{
-    const int t = (int)((ni >> 16) & 0x7F) - 64 + (int)(((mv >> 8) ^ (ni >> 23)) & 1);
-    const int kappa = (int)(mv & 0xFF) + t;
-    int u = S[(int)(uv & 0xFFFF) + t] + (int)((ni >> 8) & 0xFF);
-    int v = S[(int)(uv >> 16) + t] + (int)(ni & 0xFF);
-    if (u > v) { const int x = u; u = v; v = x; }
-    sign = (int)(((mv >> 9) ^ (ni >> 24)) & 1);
-    return go[kappa] + u * gs[kappa] - ((u * (u - 1)) >> 1) + (v - u);
 }
 
 template <int WARPS>
@@ -335,7 +271,8 @@ __device__ __forceinline__ void put_values_coop(const FillArgs &F, const RowOut 
 }
 
 // Deferred one-move elements of a row: lanes over (element, spectator)
-// pairs, groups of the next power of two >= A-1 lanes, FP64 segmented sum.
+// pairs, groups of the next power of two >= A-1 lanes, segmented sum (from
+// kLaneSets sets on: one element at a time, lanes over sets).
 // The queue holds row-relative positions, columns and packed moves
 // (bra-only a, ket-only c, sign, neutron flag in bit 31).
 template <int MODE, bool K1>
@@ -880,7 +817,7 @@ __global__ void k_fix_to_double(int64_t n, const unsigned long long *acc, double
 
 int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st)
 {
-    if (!b.dev.clist_off) return launch_rows<0>(b, nullptr, rowptr, FillArgs{}, GradArgs{}, st);
+    if (!b.dev.clist_off || b.count_walk) return launch_rows<0>(b, nullptr, rowptr, FillArgs{}, GradArgs{}, st);
     if (b.dim == 0) return CIH_OK;
     int dev = 0, sms = 148, per_sm = 1;
     cudaGetDevice(&dev);
@@ -946,6 +883,24 @@ __global__ void k_psi_fix(int64_t n, const double *psi, long long *psi_fix, int 
     }
 }
 
+// ||psi_k||^2 of each set, one block per set: above 1 + 1e-6 sets status bit 32
+// (|g_t| <= 2 ||psi||^2 must stay below the 2^7 the 2^-56 accumulators hold)
+__global__ void __launch_bounds__(1024) k_psi_norm(int64_t dim, const double *psi, int *status)
+{
+    __shared__ double part[32];
+    const double *v = psi + (int64_t)blockIdx.x * dim;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < dim; i += blockDim.x) s += v[i] * v[i];
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (threadIdx.x == 0 && !(s <= 1.0 + 1e-6)) atomicOr(status, 32);
+    }
+}
+
 int launch_grad(const cih_basis &b, const int64_t *rowptr, int K, const double *psi,
                 unsigned long long *acc, cudaStream_t st)
 {
@@ -957,7 +912,8 @@ int launch_grad(const cih_basis &b, const int64_t *rowptr, int K, const double *
         (void)cudaGetLastError();
         return fail(CIH_ERR_NOMEM, "adjoint: fixed-point vector");
     }
-    count_launches(1);
+    count_launches(2);
+    k_psi_norm<<<K, 1024, 0, st>>>(b.dim, psi, b.dev_status);
     k_psi_fix<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(n, psi, fix, b.dev_status);
     GradArgs G{K, fix, acc};
     const int rc = launch_rows<2>(b, rowptr, nullptr, FillArgs{}, G, st);

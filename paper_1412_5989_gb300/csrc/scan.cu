@@ -143,6 +143,7 @@ constexpr int64_t kStaticTileSums = 16384;                 // 128 KiB on every d
 static __device__ __align__(256) int64_t g_static_tile_sums[kStaticTileSums];
 
 // device address of the array, resolved once per device with that device current
+// (the cached address does not survive a reset of that device's primary context)
 int static_tile_sums(int device, int64_t **out)
 {
     static std::mutex mu;
@@ -177,6 +178,10 @@ extern "C" int cih_rowptr_scan_static(const int64_t *counts_dev, int64_t n, int6
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     if (n > 0 && counts_dev != rowptr_dev) {
+        // in place, or disjoint: the copy below must not read what it has written
+        const uintptr_t c0 = (uintptr_t)counts_dev, c1 = c0 + sizeof(int64_t) * (uint64_t)n;
+        const uintptr_t r0 = (uintptr_t)rowptr_dev, r1 = r0 + sizeof(int64_t) * ((uint64_t)n + 1);
+        if (c0 < r1 && r0 < c1) return fail(CIH_ERR_ARG, "rowptr_scan_static: counts and rowptr partly overlap");
         e = cudaMemcpyAsync(rowptr_dev, counts_dev, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "rowptr_scan_static: copy counts");
     }

@@ -86,3 +86,19 @@ def test_autograd_fd_density_euler(cih):
     fd = (evk[0::2, 0] - evk[1::2, 0]) / step
     err = np.abs(fd - g[idx])
     assert err.max() <= FD_ATOL, (err.max(), idx[np.argmax(err)])
+
+
+def test_adjoint_flags_an_unnormalised_vector(cih):
+    """A vector of squared norm 4 (every entry far below the per-entry bound
+    of 4) would let the fixed-point sums outgrow their range: the adjoint
+    sets the device status, which cih_check reports and clears."""
+    B = cih.Basis(2, 2, 2, 0)
+    t = torch.from_numpy(synth.tbme_table(B.tbme_len, 3)).cuda()
+    rowptr, col, val, nnz = cih.build_hamiltonian(B, t)
+    B.check()
+    psi = torch.full((B.dim,), 2.0 / np.sqrt(B.dim), dtype=torch.float64, device="cuda")
+    B.tbme_grad(rowptr, psi)
+    with pytest.raises(cih.CihError, match="status bits 32"):
+        B.check()
+    B.tbme_grad(rowptr, psi / 2.0)                           # normalised: no flag
+    B.check()

@@ -127,6 +127,8 @@ def test_entry_points_reject_bad_arguments_without_a_gpu(cih):
     assert lib.cih_set_launch(h, 16, 33) == -1
     assert lib.cih_set_launch(None, 16, 0) == -1
     assert lib.cih_set_launch(h, 8, 2) == 0 and lib.cih_set_launch(h, 16, 0) == 0
+    assert lib.cih_set_count_mode(h, 2) == -1 and lib.cih_set_count_mode(None, 0) == -1
+    assert lib.cih_set_count_mode(h, 1) == 0 and lib.cih_set_count_mode(h, 0) == 0
     rc = C.c_int32()
     # device calls refuse a host-only handle
     assert lib.cih_ham_count(h, C.c_void_p(16), None, None) == -1
