@@ -11,17 +11,36 @@
 //     element-major x[i * K + s], FP64;
 //   - full reorthogonalisation: classical Gram-Schmidt applied twice, dot
 //     products reduced in two fixed-order stages.
-// Host: per set, the lowest Ritz values of the tridiagonal by bisection, the
-// residual bounds beta_m |z_m| and the lowest Ritz vector's coefficients by
-// inverse iteration.
+// Host: per set (sets on parallel host threads), the lowest Ritz values and
+// the residual bounds beta_m |z_m| from implicit-QR sweeps of the tridiagonal
+// that rotate only the last row of its eigenvector matrix; the lowest Ritz
+// vector's coefficients by inverse iteration.
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "cih_internal.h"
 
 namespace cih {
 namespace {
+
+// fn(s) for s = 0 .. K - 1, on up to 8 host threads when there is more than one set
+template <class F>
+void parallel_sets(int K, F &&fn)
+{
+    const int nt = std::min({K, 8, (int)std::max(1u, std::thread::hardware_concurrency())});
+    if (nt <= 1) {
+        for (int s = 0; s < K; ++s) fn(s);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&, t]() {
+            for (int s = t; s < K; s += nt) fn(s);
+        });
+    for (auto &x : th) x.join();
+}
 
 constexpr int kDotBlocks = 256;
 constexpr int kThreads = 256;
@@ -448,31 +467,32 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
         }
         if (rc || (rc = dots(w, 1, w))) break;
         m = j + 1;
-        bool all = true;
-        for (int s = 0; s < K; ++s) {
+        // per set (sets in parallel on host threads): Ritz values and residual
+        // bounds beta_m |z_m| of the lowest nev, from the tridiagonal's QR
+        // eigen-decomposition (last eigenvector components)
+        parallel_sets(K, [&](int s) {
             fh[s] = 0.0;
-            if (done[s]) continue;
+            if (done[s]) return;
             const double bj = std::sqrt(std::max(hh[s], 0.0));
             beta[s].push_back(bj);
             const int ms = m_of[s] = (int)alpha[s].size();
-            // Ritz values and residual bounds beta_m |z_m| of the lowest nev
             const int nv = std::min(nev, ms);
             bool conv = ms >= std::min<int64_t>(nev, dim);
             const bool invariant = bj <= 1e-12 * (std::fabs(alpha[s].back()) + 1.0);
-            std::vector<double> z(ms);
+            std::vector<double> dq(alpha[s]), eq(beta[s].begin(), beta[s].begin() + (ms - 1)), zl;
+            if (eq.empty()) eq.push_back(0.0);
+            tridiag_qr_last(ms, dq, eq, zl);
             for (int r = 0; r < nv; ++r) {
-                const double th = tridiag_eigenvalue(ms, alpha[s].data(), beta[s].data(), r);
+                const double th = dq[r];
                 theta[(size_t)s * nev + r] = th;
-                if (conv && !invariant) {
-                    tridiag_eigenvector(ms, alpha[s].data(), beta[s].data(), th, z.data());
-                    if (bj * std::fabs(z[ms - 1]) > tol * std::max(1.0, std::fabs(th))) conv = false;
-                }
+                if (conv && !invariant && bj * std::fabs(zl[r]) > tol * std::max(1.0, std::fabs(th))) conv = false;
             }
             met[s] = conv || invariant;
             if (met[s] || ms == m_max) done[s] = 1;
             else fh[s] = 1.0 / bj;                                  // next vector; frozen sets get zeros
-            all = all && done[s];
-        }
+        });
+        bool all = true;
+        for (int s = 0; s < K; ++s) all = all && done[s];
         if (all) break;
         scale(w, V + (int64_t)(j + 1) * vstride);
     }

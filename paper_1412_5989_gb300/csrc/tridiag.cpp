@@ -10,12 +10,13 @@ namespace cih {
 
 // Symmetric tridiagonal eigenproblem (diagonal d, off-diagonal e) by
 // implicit QR steps with Wilkinson shifts, chasing the bulge with Givens
-// rotations; Z accumulates the rotations (column k = eigenvector k).
-// Eigenvalues returned ascending with their vectors.
-void tridiag_qr(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &Z)
+// rotations.  Each rotation of columns (k, k + 1) is applied to the rows of
+// Z listed in `rows` (all n rows: the eigenvectors; only the last: their last
+// components, which is all the Lanczos residual bounds need).  Eigenvalues
+// are returned ascending, Z's columns permuted to match.
+static void qr_sweeps(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &Z, int row0)
 {
-    Z.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
+    const int nrows = n - row0;
     const double eps = 2.220446049250313e-16;
     int hi = n - 1, guard = 0;
     while (hi > 0 && guard < 64 * n + 100) {
@@ -44,7 +45,7 @@ void tridiag_qr(int n, std::vector<double> &d, std::vector<double> e, std::vecto
                 z = s * e[k + 1];
                 e[k + 1] *= c;
             }
-            for (int i = 0; i < n; ++i) {
+            for (int i = 0; i < nrows; ++i) {
                 double zk = Z[(size_t)i * n + k], zk1 = Z[(size_t)i * n + k + 1];
                 Z[(size_t)i * n + k] = c * zk + s * zk1;
                 Z[(size_t)i * n + k + 1] = -s * zk + c * zk1;
@@ -54,44 +55,29 @@ void tridiag_qr(int n, std::vector<double> &d, std::vector<double> e, std::vecto
     std::vector<int> ord(n);
     std::iota(ord.begin(), ord.end(), 0);
     std::sort(ord.begin(), ord.end(), [&](int a, int b) { return d[a] < d[b]; });
-    std::vector<double> d2(n), Z2((size_t)n * n);
+    std::vector<double> d2(n), Z2((size_t)nrows * n);
     for (int j = 0; j < n; ++j) {
         d2[j] = d[ord[j]];
-        for (int i = 0; i < n; ++i) Z2[(size_t)i * n + j] = Z[(size_t)i * n + ord[j]];
+        for (int i = 0; i < nrows; ++i) Z2[(size_t)i * n + j] = Z[(size_t)i * n + ord[j]];
     }
     d.swap(d2);
     Z.swap(Z2);
 }
 
-// Number of eigenvalues of the tridiagonal (d, e) below x: negative pivots of
-// the LDL^T factorisation of T - x I (Sylvester's law of inertia).
-static int count_below(int n, const double *d, const double *e, double x)
+void tridiag_qr(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &Z)
 {
-    int neg = 0;
-    double q = 1.0;
-    for (int k = 0; k < n; ++k) {
-        q = d[k] - x - (k ? e[k - 1] * e[k - 1] / q : 0.0);
-        if (q == 0.0) q = -1e-300;
-        neg += q < 0.0;
-    }
-    return neg;
+    Z.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
+    qr_sweeps(n, d, std::move(e), Z, 0);
 }
 
-// r-th smallest eigenvalue by bisection between Gershgorin bounds
-double tridiag_eigenvalue(int n, const double *d, const double *e, int r)
+// Eigenvalues ascending (into d) and the last component of each eigenvector
+// (into zlast): the QR sweeps above with only the last row of Z rotated.
+void tridiag_qr_last(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &zlast)
 {
-    double lo = d[0], hi = d[0];
-    for (int k = 0; k < n; ++k) {
-        const double rad = (k ? std::fabs(e[k - 1]) : 0.0) + (k + 1 < n ? std::fabs(e[k]) : 0.0);
-        lo = std::min(lo, d[k] - rad);
-        hi = std::max(hi, d[k] + rad);
-    }
-    for (int it = 0; it < 300; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (count_below(n, d, e, mid) > r) hi = mid; else lo = mid;
-    }
-    return 0.5 * (lo + hi);
+    zlast.assign((size_t)n, 0.0);
+    zlast[(size_t)n - 1] = 1.0;
+    qr_sweeps(n, d, std::move(e), zlast, n - 1);
 }
 
 // normalised eigenvector for the eigenvalue estimate theta: three steps of
