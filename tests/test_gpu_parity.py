@@ -71,6 +71,23 @@ def test_whole_matrix_mid(cih):
     assert_values(val[0].cpu().numpy(), val_o)
 
 
+@pytest.mark.parametrize("sp", [(3, 3, 2, 0), (2, 1, 3, 1), (3, 3, 4, 0), (4, 4, 4, 0)])
+def test_count_walk_against_oracle(cih, sp):
+    """The count pass's walk form -- the one a basis without count lists
+    (bucket directory above 4096 entries, or above 63 levels) runs -- selected
+    with cih_set_count_mode: row counts equal to the oracle's, row pointers
+    equal to the count-list form's."""
+    B = cih.Basis(*sp)
+    S = oracle.Space(*sp)
+    rp_lists, nnz_lists = B.count()
+    B.set_count_mode(True)
+    rp_walk, nnz_walk = B.count()
+    B.check()
+    B.set_count_mode(False)
+    np.testing.assert_array_equal(np.diff(rp_walk.cpu().numpy()), S.count_rows())
+    assert nnz_walk == nnz_lists and torch.equal(rp_walk, rp_lists)
+
+
 def test_empty_basis(cih):
     B = cih.Basis(2, 2, 2, 1)
     assert B.dim == 0
@@ -245,27 +262,96 @@ def test_gradient_full_path_mid(cih):
     assert e1 + float(g @ t.astype(np.float64)) == pytest.approx(ev[0][0], rel=1e-6)
 
 
+def _torch_lanczos(matvec, dim, nev, iters, seed):
+    """Plain FP64 Lanczos in torch with full reorthogonalisation (classical
+    Gram-Schmidt twice) from a seeded normal start: the nev lowest Ritz
+    values and vectors of the last step, and the residual bounds."""
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    v = torch.randn(dim, dtype=torch.float64, device="cuda", generator=g)
+    V = torch.empty((iters + 1, dim), dtype=torch.float64, device="cuda")
+    V[0] = v / torch.linalg.vector_norm(v)
+    al, be = [], []
+    m = 0
+    for j in range(iters):
+        w = matvec(V[j])
+        for _ in range(2):
+            h = V[: j + 1] @ w
+            w -= V[: j + 1].T @ h
+            if _ == 0:
+                al.append(float(h[j]))
+            else:
+                al[-1] += float(h[j])
+        b = float(torch.linalg.vector_norm(w))
+        m = j + 1
+        if b < 1e-12:
+            break
+        be.append(b)
+        V[j + 1] = w / b
+        if m >= nev and m % 20 == 0:                 # stop once the nev residual bounds are small
+            T = np.diag(al) + np.diag(be[: m - 1], 1) + np.diag(be[: m - 1], -1)
+            th, Z = np.linalg.eigh(T)
+            if np.all(b * np.abs(Z[-1, :nev]) <= 1e-8 * np.abs(th[:nev])):
+                break
+    T = np.diag(al) + np.diag(be[: m - 1], 1) + np.diag(be[: m - 1], -1)
+    th, Z = np.linalg.eigh(T)
+    Y = torch.from_numpy(Z[:, :nev].copy()).cuda().T @ V[:m]
+    return th[:nev], Y
+
+
 def test_lanczos_residual_full_size(cih):
-    """4+4 Nmax=6 (925 M stored nonzeros), too large for the oracle's Lanczos:
-    the lowest Ritz pair's residual |H psi - E0 psi| computed independently in
-    torch from the stored half (row part + mirrored part - diagonal)."""
+    """4+4 Nmax=6 (925 M stored nonzeros), too large for the oracle's Lanczos.
+    The library's five lowest eigenvalues against an independent FP64 Lanczos
+    in torch whose products are built from the stored half (row part +
+    mirrored part - diagonal); the true residual |H y - theta y| of each of
+    that run's five lowest Ritz pairs, and of the library's lowest Ritz vector."""
     sp = (4, 4, 6, 0)
     B = cih.Basis(*sp)
     t = synth.tbme_table(B.tbme_len, 0)
     rowptr, col, val, nnz = cih.build_hamiltonian(B, torch.from_numpy(t).cuda())
-    ev, psi, conv = B.lanczos(rowptr, col, val, nev=1, max_iter=600, tol=1e-9)
+    ev, psi, conv = B.lanczos(rowptr, col, val, nev=5, max_iter=600, tol=1e-9)
     assert conv
-    x = psi[0]
     v = val[0].double()
+    del val
     rows = torch.repeat_interleave(torch.arange(B.dim, device="cuda"), rowptr[1:] - rowptr[:-1])
     c = col.long()
-    y = torch.zeros(B.dim, dtype=torch.float64, device="cuda")
-    y.index_add_(0, rows, v * x[c])                                  # upper half
-    y.index_add_(0, c, v * x[rows])                                  # mirrored half
+    del col
     diag = rowptr[:-1]
-    y -= v[diag] * x                                                 # the diagonal counted once
-    res = float(torch.linalg.vector_norm(y - ev[0][0] * x))
+    vd = v[diag]
+
+    def matvec(x):
+        y = torch.zeros(B.dim, dtype=torch.float64, device="cuda")
+        y.index_add_(0, rows, v * x[c])                              # upper half
+        y.index_add_(0, c, v * x[rows])                              # mirrored half
+        return y - vd * x                                            # the diagonal counted once
+
+    x = psi[0]
     assert abs(float(torch.linalg.vector_norm(x)) - 1.0) < 1e-10
-    assert res <= 1e-6 * abs(ev[0][0]), res
-    del rows, c, v, y, col, val
+    res0 = float(torch.linalg.vector_norm(matvec(x) - ev[0][0] * x))
+    assert res0 <= 1e-6 * abs(ev[0][0]), res0
+    th, Y = _torch_lanczos(matvec, B.dim, 5, 400, 11)
+    for k in range(5):
+        y = Y[k] / torch.linalg.vector_norm(Y[k])
+        res = float(torch.linalg.vector_norm(matvec(y) - th[k] * y))
+        assert res <= 1e-5 * abs(th[k]), (k, res)
+    np.testing.assert_allclose(ev[0], th, rtol=1e-5)
+    del rows, c, v, Y
+    torch.cuda.empty_cache()
+
+
+def test_lanczos_5p6n_against_oracle(cih):
+    """5+6 Nmax=4, 2M=1 (the uneven batch's third instance, seed 102; 207 M
+    stored nonzeros): the library's five lowest eigenvalues against the
+    oracle's Lanczos run on the GPU-built matrix."""
+    sp = (5, 6, 4, 1)
+    B = cih.Basis(*sp)
+    t = synth.tbme_table(B.tbme_len, 102)
+    rowptr, col, val, nnz = cih.build_hamiltonian(B, torch.from_numpy(t).cuda())
+    B.check()
+    ev, _, conv = B.lanczos(rowptr, col, val, nev=5, max_iter=500, tol=1e-9)
+    assert conv
+    ev_o, _, _, conv_o = oracle.lanczos(rowptr.cpu().numpy(), col.cpu().numpy(), val[0].cpu().numpy(),
+                                        nev=5, max_iter=500, tol=1e-10)
+    assert conv_o
+    np.testing.assert_allclose(ev[0], ev_o, rtol=1e-5)
+    del col, val
     torch.cuda.empty_cache()
