@@ -40,7 +40,8 @@ def _stale(target, deps):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(SRC, "cih_internal.h"), os.path.join(ROOT, "include", "cih.h")]
+    headers = [os.path.join(SRC, "cih_internal.h"), os.path.join(SRC, "ham_common.cuh"),
+               os.path.join(ROOT, "include", "cih.h")]
     objs, jobs = [], []
     for s in SOURCES:
         src = os.path.join(SRC, s)
