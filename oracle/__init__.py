@@ -75,6 +75,11 @@ def _load():
     lib.or_tridiag_eig.restype = C.c_double
     lib.or_tridiag_eig.argtypes = [C.c_int, dp, dp, C.c_int]
     lib.or_grad_elementwise.argtypes = [P, i64p, ip, dp, dp]
+    lib.or_onebody_index.restype = C.c_longlong
+    lib.or_onebody_index.argtypes = [P, C.c_int, C.c_int]
+    lib.or_onebody_len.restype = C.c_longlong
+    lib.or_onebody_len.argtypes = [P]
+    lib.or_set_onebody.argtypes = [P, dp]
     _lib = lib
     return lib
 
@@ -192,6 +197,32 @@ class Space:
         s = C.c_int()
         idx = self._lib.or_tbme_index(self._h, a, b, c, d, C.byref(s))
         return idx, s.value
+
+    # ---- one-body table ---------------------------------------------
+    @property
+    def onebody_len(self) -> int:
+        """Entries of the one-body table: per species, groups of orbitals with
+        equal (2m, N parity), each storing its packed upper triangle."""
+        return self._lib.or_onebody_len(self._h)
+
+    def onebody_index(self, a: int, c: int) -> int:
+        """Table index of t_ac (either order) for combined orbitals, -1 if
+        a and c are not one species with equal 2m and N parity."""
+        return self._lib.or_onebody_index(self._h, a, c)
+
+    def set_onebody(self, t1=None):
+        """Use the one-body table t1 (onebody_len float64) as the one-body part
+        of H, H = sum t_ac a+_a a_c + V, for every later matrix call; None
+        returns to e_a = hbar_omega (N_a + 3/2) or the per-orbital table."""
+        if t1 is None:
+            self._t1 = None
+            self._lib.or_set_onebody(self._h, None)
+            return
+        t1 = np.ascontiguousarray(t1, dtype=np.float64)
+        if t1.shape != (self.onebody_len,):
+            raise ValueError("one-body table needs onebody_len entries")
+        self._t1 = t1                                   # kept alive while in use
+        self._lib.or_set_onebody(self._h, _ptr(t1, C.c_double))
 
     # ---- matrix -----------------------------------------------------
     @staticmethod

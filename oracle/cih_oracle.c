@@ -19,7 +19,11 @@
  *   - Slater determinant |Phi> = a+_{i1} ... a+_{iA} |0>, i1 < ... < iA in the
  *     combined index (proton orbitals first, then neutron orbitals);
  *   - H = sum_a e_a a+_a a_a + sum_{a<b, c<d} V_{ab,cd} a+_a a+_b a_d a_c,
- *     e_a = hbar_omega (N_a + 3/2) unless a per-orbital table is given;
+ *     e_a = hbar_omega (N_a + 3/2) unless a per-orbital table is given; or,
+ *     with a one-body table t (or_set_onebody), H = sum_{a,c} t_ac a+_a a_c +
+ *     the same two-body part, t symmetric and nonzero only between orbitals
+ *     of one species with equal 2m and equal N parity (the paper's MFDn reads
+ *     its one-body operator, the kinetic energy, from file: Sec. 2);
  *   - V_{ab,cd} is one real parameter that stands for both V_{ab,cd} and
  *     V_{cd,ab} (Hermiticity); a swapped pair changes its sign (antisymmetry).
  *
@@ -61,6 +65,15 @@ typedef struct {
     or_chan ch[3];            /* 0 = pp, 1 = nn, 2 = pn                      */
     long long tbme_len;
     int *pair_chan, *pair_grp, *pair_loc;   /* ntot x ntot lookup            */
+    /* one-body layout: groups of orbitals of one species with equal (2m, N
+       parity), in the order (species, 2m, parity) ascending, members ascending;
+       each group stores its packed upper triangle (a <= c) */
+    int ob_ngroups;
+    int *ob_grp, *ob_loc;     /* per combined orbital: group, place in it      */
+    int *ob_gsize, *ob_gfirst, *ob_orb;     /* group size, first member, members */
+    long long *ob_goff;       /* offset of each group's triangle              */
+    long long ob_len;
+    const double *t1;         /* the one-body table in use, or NULL           */
 } or_space;
 
 /* ------------------------------------------------------------------ */
@@ -170,6 +183,7 @@ void or_space_free(or_space *S)
     free(S->nbeg); free(S->ncnt); free(S->base);
     for (int c = 0; c < 3; c++) free_chan(&S->ch[c]);
     free(S->pair_chan); free(S->pair_grp); free(S->pair_loc);
+    free(S->ob_grp); free(S->ob_loc); free(S->ob_gsize); free(S->ob_gfirst); free(S->ob_orb); free(S->ob_goff);
     free(S);
 }
 
@@ -261,6 +275,64 @@ static void build_channel(or_space *S, int c)
     C->len = off;
     free(pa); free(pb);
 }
+
+/* One-body table layout (see or_space).  Plain quadratic scans over the
+   orbitals: a group is every orbital of species s with the key (2m, parity). */
+static void build_onebody_layout(or_space *S)
+{
+    int nt = S->ntot > 0 ? S->ntot : 1;
+    S->ob_grp = (int *)malloc(sizeof(int) * nt);
+    S->ob_loc = (int *)malloc(sizeof(int) * nt);
+    S->ob_orb = (int *)malloc(sizeof(int) * nt);
+    S->ob_gsize = (int *)malloc(sizeof(int) * nt);
+    S->ob_gfirst = (int *)malloc(sizeof(int) * nt);
+    S->ob_goff = (long long *)malloc(sizeof(long long) * nt);
+    for (int a = 0; a < S->ntot; a++) S->ob_grp[a] = -1;
+    int g = 0, placed = 0;
+    long long off = 0;
+    for (int s = 0; s < 2; s++) {
+        int base = s ? S->norb[0] : 0;
+        for (int m2 = -4 * ORW * 64; m2 <= 4 * ORW * 64; m2++)        /* 2m ascending */
+            for (int par = 0; par < 2; par++) {
+                int n = 0;
+                for (int a = 0; a < S->norb[s]; a++) {
+                    const or_orb *o = &S->orb[s][a];
+                    if (o->m2 != m2 || (o->N & 1) != par) continue;
+                    S->ob_grp[base + a] = g;
+                    S->ob_loc[base + a] = n;
+                    S->ob_orb[placed + n] = base + a;
+                    n++;
+                }
+                if (!n) continue;
+                S->ob_gsize[g] = n;
+                S->ob_gfirst[g] = placed;
+                S->ob_goff[g] = off;
+                off += (long long)n * (n + 1) / 2;
+                placed += n;
+                g++;
+            }
+    }
+    S->ob_ngroups = g;
+    S->ob_len = off;
+}
+
+/* table index of t_ac (either order), or -1 if a and c are not in one group */
+long long or_onebody_index(const or_space *S, int a, int c)
+{
+    if (a < 0 || c < 0 || a >= S->ntot || c >= S->ntot) return -1;
+    int g = S->ob_grp[a];
+    if (g < 0 || g != S->ob_grp[c]) return -1;
+    long long u = S->ob_loc[a], v = S->ob_loc[c];
+    if (u > v) { long long t = u; u = v; v = t; }
+    long long n = S->ob_gsize[g];
+    return S->ob_goff[g] + u * n - u * (u - 1) / 2 + (v - u);
+}
+
+long long or_onebody_len(const or_space *S) { return S->ob_len; }
+
+/* use t (ob_len doubles, kept alive by the caller) as the one-body part of H
+   for later element, dense and row calls; NULL returns to e_a / hbar_omega */
+void or_set_onebody(or_space *S, const double *t1) { S->t1 = t1; }
 
 or_space *or_space_new(int Zp, int Zn, int Nmax, int twoM)
 {
@@ -376,6 +448,7 @@ or_space *or_space_new(int Zp, int Zn, int Nmax, int twoM)
             }
     }
     S->tbme_len = tot;
+    build_onebody_layout(S);
     return S;
 }
 
@@ -552,6 +625,7 @@ long long or_tbme_index(const or_space *S, int a, int b, int c, int d, int *sign
 
 static double one_body(const or_space *S, const double *esp, double hw, int a)
 {
+    if (S->t1) return S->t1[or_onebody_index(S, a, a)];
     if (esp) return esp[a];
     return hw * (orb_N(S, a) + 1.5);
 }
@@ -606,6 +680,11 @@ int or_element(const or_space *S, const float *tbme, const double *esp, double h
         memcpy(t, oj, sizeof(t));
         int s = annihilate(t, c);
         s *= create(t, a);                    /* a+_a a_c |Phi_j> = s |Phi_i> */
+        if (S->t1) {                          /* the one-body term first */
+            long long k1 = or_onebody_index(S, a, c);
+            if (k1 < 0) return -1;
+            sum += S->t1[k1];
+        }
         for (int k = 0; k < S->ntot; k++) {
             if (!occ_bit(oj, k) || k == c) continue;     /* spectators, ascending */
             if (vlookup(S, tbme, a, k, c, k, &v)) return -1;
@@ -640,6 +719,23 @@ int or_dense_brute(const or_space *S, const float *tbme, const double *esp, doub
         state_occ(S, j, o);
         for (int a = 0; a < S->ntot; a++)
             if (occ_bit(o, a)) H[j * D + j] += one_body(S, esp, hw, a);
+        if (S->t1)                            /* t_ac a+_a a_c, a != c, both orders */
+            for (int g = 0; g < S->ob_ngroups; g++) {
+                int n = S->ob_gsize[g];
+                for (int u = 0; u < n; u++)
+                    for (int w = 0; w < n; w++) {
+                        if (u == w) continue;
+                        int a = S->ob_orb[S->ob_gfirst[g] + u], c = S->ob_orb[S->ob_gfirst[g] + w];
+                        memcpy(t, o, sizeof(t));
+                        int s = annihilate(t, c);
+                        if (!s) continue;
+                        s *= create(t, a);
+                        if (!s) continue;
+                        long long i = occ_index(S, t);
+                        if (i < 0) continue;
+                        H[i * D + j] += s * S->t1[or_onebody_index(S, a, c)];
+                    }
+            }
         for (int c3 = 0; c3 < 3; c3++) {
             const or_chan *C = &S->ch[c3];
             for (int g = 0; g < C->ngroups; g++) {

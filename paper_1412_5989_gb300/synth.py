@@ -27,3 +27,9 @@ def tbme_tables(length: int, seeds) -> np.ndarray:
 def single_particle_energies(n: int, seed: int, scale: float = 10.0) -> np.ndarray:
     """Per-orbital one-body energies (float64), uniform in [0, scale)."""
     return np.random.Generator(np.random.PCG64(seed)).uniform(0.0, scale, n)
+
+
+def onebody_table(length: int, seed: int) -> np.ndarray:
+    """One synthetic one-body table: ``length`` standard-normal float64 draws,
+    one per packed table entry in table order (the caller's layout)."""
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal(length)

@@ -419,3 +419,100 @@ def test_gradient(Z, N):
         Ep = np.linalg.eigvalsh(H + h * dH)[0]
         Em = np.linalg.eigvalsh(H - h * dH)[0]
         assert (Ep - Em) / (2 * h) == pytest.approx(g[k], abs=1e-6)
+
+
+# ---------------------------------------------------------------- one-body table
+
+def _t_full(S, t1):
+    """The symmetric one-body matrix t[a, c] written out from the table
+    (zero outside the one-species, equal-2m, equal-parity groups)."""
+    n = S.norb[0] + S.norb[1]
+    T = np.zeros((n, n))
+    for a in range(n):
+        for c in range(n):
+            k = S.onebody_index(a, c)
+            if k >= 0:
+                T[a, c] = t1[k]
+    return T
+
+
+def test_onebody_layout_groups():
+    """t_ac has an entry exactly when a and c are one species with equal 2m
+    and equal N parity; the packed triangles tile the table."""
+    S = oracle.Space(3, 2, 3, 1)
+    o = np.concatenate([S.orbitals(0), S.orbitals(1)])
+    sp = np.array([0] * S.norb[0] + [1] * S.norb[1])
+    n = len(o)
+    seen = set()
+    for a in range(n):
+        for c in range(n):
+            k = S.onebody_index(a, c)
+            same = sp[a] == sp[c] and o[a, 3] == o[c, 3] and (o[a, 0] - o[c, 0]) % 2 == 0
+            assert (k >= 0) == same
+            if same:
+                assert k == S.onebody_index(c, a)
+                seen.add(k)
+    assert seen == set(range(S.onebody_len))
+
+
+@pytest.mark.parametrize("Z,N,Nmax,twoM", [(1, 0, 3, 1), (0, 1, 4, 3), (1, 0, 4, -1)])
+def test_onebody_single_particle_block(Z, N, Nmax, twoM):
+    """One particle: H is the one-body matrix itself on the orbitals of the
+    basis (closed form), whatever the two-body table."""
+    S = oracle.Space(Z, N, Nmax, twoM)
+    t1 = synth.onebody_table(S.onebody_len, 3)
+    S.set_onebody(t1)
+    T = _t_full(S, t1)
+    orb = [o[0] for o in occupations(S)]
+    want = T[np.ix_(orb, orb)]
+    for H in (S.dense_sc(synth.tbme_table(S.tbme_len, 1)), S.dense_brute(synth.tbme_table(S.tbme_len, 1))):
+        np.testing.assert_allclose(H, want, rtol=0, atol=1e-14)
+    assert np.abs(want - np.diag(np.diag(want))).max() > 0.1      # off-diagonal (Delta N = 2) couplings present
+
+
+@pytest.mark.parametrize("Z,N", [(2, 0), (0, 2), (1, 1)])
+def test_onebody_two_particle_formula(Z, N):
+    """Two particles, no two-body part: <ab|T|cd> = t_ac d_bd - t_ad d_bc -
+    t_bc d_ad + t_bd d_ac for a<b, c<d (textbook, with t = 0 across species)."""
+    S = oracle.Space(Z, N, 3, 0)
+    t1 = synth.onebody_table(S.onebody_len, 8)
+    S.set_onebody(t1)
+    T = _t_full(S, t1)
+    H = S.dense_sc(np.zeros(S.tbme_len, np.float32))
+    occ = occupations(S)
+    for i, (a, b) in enumerate(occ):
+        for j, (c, d) in enumerate(occ):
+            want = T[a, c] * (b == d) - T[a, d] * (b == c) - T[b, c] * (a == d) + T[b, d] * (a == c)
+            assert H[i, j] == pytest.approx(want, abs=1e-13)
+
+
+@pytest.mark.parametrize("Z,N,Nmax,twoM", [(2, 2, 2, 0), (3, 3, 2, 0), (2, 1, 3, 1), (3, 2, 2, 3), (1, 2, 3, 7)])
+def test_onebody_slater_condon_equals_operator_application(Z, N, Nmax, twoM):
+    S = oracle.Space(Z, N, Nmax, twoM)
+    S.set_onebody(synth.onebody_table(S.onebody_len, 4))
+    t = synth.tbme_table(S.tbme_len, 6)
+    Hb = S.dense_brute(t)
+    Hs = S.dense_sc(t)
+    np.testing.assert_allclose(Hs, Hb, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(Hb, Hb.T, rtol=0, atol=1e-12)   # Hermiticity
+    rp, col, val = S.half_csr(t)                               # the row walk agrees
+    Hh = np.zeros_like(Hs)
+    for i in range(S.dim):
+        Hh[i, col[rp[i]:rp[i + 1]]] = val[rp[i]:rp[i + 1]]
+    np.testing.assert_allclose(np.triu(Hs), Hh, rtol=1e-6, atol=1e-5)
+
+
+def test_onebody_diagonal_table_equals_orbital_energies():
+    """A one-body table with only its diagonal set (t_aa = e_a) gives the
+    same matrix as the per-orbital energies."""
+    S = oracle.Space(3, 3, 2, 0)
+    n = S.norb[0] + S.norb[1]
+    esp = synth.single_particle_energies(n, 5)
+    t1 = np.zeros(S.onebody_len)
+    for a in range(n):
+        t1[S.onebody_index(a, a)] = esp[a]
+    t = synth.tbme_table(S.tbme_len, 2)
+    S.set_onebody(t1)
+    H1 = S.dense_sc(t)
+    S.set_onebody(None)
+    np.testing.assert_array_equal(H1, S.dense_sc(t, esp))
