@@ -150,6 +150,52 @@ int cih_ham_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hba
                  const float *tbme_dev, const double *e_sp_dev,
                  int32_t *col_dev, float *val_dev, void *stream);
 
+/* One-body table (Sec. 2: MFDn reads its one-body operator, the kinetic
+ * energy, from file): with it, H = sum_{a,c} t_ac a+_a a_c + the two-body
+ * part, in place of the orbital energies e_a.  t is symmetric and has entries
+ * only for orbitals a, c of one species with equal 2m and equal N parity
+ * (Delta N = 2 couplings included).  Layout: per species (protons first),
+ * groups of such orbitals ordered by (2m, parity) ascending, members in
+ * ascending orbital order; a group stores its packed row-major upper triangle
+ * (u <= v at group_offset + u*n - u(u-1)/2 + (v-u)), one double each.
+ * cih_onebody_info: *len = entries of the table.
+ * cih_onebody_index: *index of t_ac for combined orbitals a, c in either
+ * order, -1 if a and c are not one group.  Host-side; any handle.
+ * Errors: CIH_ERR_ARG (NULL). */
+int cih_onebody_info(cih_basis_h h, int64_t *len);
+int cih_onebody_index(cih_basis_h h, int32_t a, int32_t c, int64_t *index);
+
+/* As cih_ham_fill with a one-body table (layout above; onebody_dev: len
+ * double, device, shared by the K sets) in place of the orbital energies:
+ * the diagonal holds sum over occupied a of t_aa plus the two-body pairs, and
+ * a one-particle move a <- c holds its sign times (t_ac + the spectator sum).
+ * Values and their summation as cih_ham_fill.  Errors as cih_ham_fill. */
+int cih_ham_fill_onebody(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, const float *tbme_dev,
+                         const double *onebody_dev, int32_t *col_dev, float *val_dev, void *stream);
+
+/* Row-sharded fill (Sec. 2 and 4.1: the matrix is split into row chunks of
+ * about equal nonzero counts, one per process): the fill of rows r0 .. r1 - 1
+ * only, written to arrays that hold just those rows.  With nnz_s =
+ * rowptr[r1] - rowptr[r0], stored nonzero e of those rows goes to
+ * col_dev[e - rowptr[r0]] (nnz_s int32) and its value for set k to
+ * val_dev[k * nnz_s + e - rowptr[r0]] (K x nnz_s float).  rowptr_dev is the
+ * whole row-pointer array from cih_ham_count (device, dim + 1 int64); the
+ * other arguments as cih_ham_fill.  The shards of any partition of 0 .. dim
+ * concatenate to cih_ham_fill's arrays bit for bit.  0 <= r0 <= r1 <= dim;
+ * r0 == r1 does nothing.  Errors: CIH_ERR_ARG, CIH_ERR_CUDA. */
+int cih_ham_fill_rows(cih_basis_h h, const int64_t *rowptr_dev, int64_t r0, int64_t r1, int32_t K,
+                      double hbar_omega, const float *tbme_dev, const double *e_sp_dev, int32_t *col_dev,
+                      float *val_dev, void *stream);
+
+/* Row boundaries of nshards shards of about equal stored nonzeros (Sec. 4.1's
+ * balancing of chunks by nonzero count), from a host copy of the row pointers
+ * (rowptr_host: dim + 1 int64): bounds_host[0] = 0 <= bounds_host[1] <= ... <=
+ * bounds_host[nshards] = dim (nshards + 1 int64, host); shard k is rows
+ * bounds[k] .. bounds[k + 1] - 1, starting at the first row whose elements
+ * begin at or after k/nshards of the nonzeros.  Host only.
+ * Errors: CIH_ERR_ARG. */
+int cih_shard_rows(const int64_t *rowptr_host, int64_t dim, int32_t nshards, int64_t *bounds_host);
+
 /* As cih_ham_fill, with the K tables interleaved element-major
  * (tbme_il_dev[t * K + k] = entry t of set k; see cih_tbme_interleave), so that
  * the K values of one nonzero come from one contiguous read.  Output layout as

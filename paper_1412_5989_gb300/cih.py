@@ -46,6 +46,11 @@ _SIGS = {
     "cih_ham_count": [_P, _P, _i64p, _P],
     "cih_ham_fill": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
     "cih_ham_fill_interleaved": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
+    "cih_ham_fill_rows": [_P, _P, C.c_int64, C.c_int64, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
+    "cih_shard_rows": [_i64p, C.c_int64, C.c_int32, _i64p],
+    "cih_onebody_info": [_P, _i64p],
+    "cih_onebody_index": [_P, C.c_int32, C.c_int32, _i64p],
+    "cih_ham_fill_onebody": [_P, _P, C.c_int32, _P, _P, _P, _P, _P],
     "cih_ham_fill_batched": [_P, _P, C.c_int32, C.c_double, _P, _P, _P, _P, _P],
     "cih_tbme_interleave": [C.c_int32, C.c_int64, _P, _P, _P],
     "cih_ham_build_host": [_P, C.c_int32, C.c_double, _P, _P, _P, _P, _P, C.c_int64, _i64p, _P],
@@ -128,6 +133,17 @@ def rowptr_scan_static(counts, rowptr=None, stream=None):
     return rowptr
 
 
+def shard_bounds(rowptr_host, nshards: int) -> np.ndarray:
+    """Row boundaries of nshards shards of about equal stored nonzeros
+    (cih_shard_rows): rowptr_host is a host copy (numpy or CPU tensor) of the
+    row pointers; returns int64 (nshards + 1,)."""
+    rp = np.ascontiguousarray(np.asarray(rowptr_host), dtype=np.int64)
+    out = np.zeros(nshards + 1, dtype=np.int64)
+    _ok(lib.cih_shard_rows(rp.ctypes.data_as(_i64p), len(rp) - 1, nshards, out.ctypes.data_as(_i64p)),
+        "shard_rows")
+    return out
+
+
 def tbme_interleave(tbme, stream=None):
     """Element-major copy of K tables: out[t * K + k] = tbme[k, t] (device)."""
     import torch
@@ -200,6 +216,34 @@ class Basis:
         return dict(orbitals=orbs[:ntot], bits_p=bp[: self.n_sd[0]], bits_n=bn[: self.n_sd[1]],
                     nbeg=nb[: self.n_sd[0]], ncnt=nc[: self.n_sd[0]], rowbase=rb)
 
+    @property
+    def onebody_len(self) -> int:
+        """Entries of the one-body table (cih_onebody_info)."""
+        n = C.c_int64()
+        _ok(lib.cih_onebody_info(self._h, C.byref(n)), "onebody_info")
+        return n.value
+
+    def onebody_index(self, a: int, c: int) -> int:
+        """Index of t_ac in the one-body table, -1 if a, c are not one group."""
+        idx = C.c_int64()
+        _ok(lib.cih_onebody_index(self._h, a, c, C.byref(idx)), "onebody_index")
+        return idx.value
+
+    def fill_onebody(self, rowptr, nnz: int, tbme, onebody, stream=None, col=None, val=None):
+        """Fill pass with a one-body table (onebody_len float64, CUDA or host)
+        in place of the orbital energies (cih_ham_fill_onebody).  Returns
+        (col int32[nnz], val float32[K, nnz])."""
+        import torch
+        t = self._check_table(tbme)
+        K = t.shape[0]
+        t1 = torch.as_tensor(onebody, dtype=torch.float64).to("cuda").contiguous()
+        if t1.numel() != self.onebody_len:
+            raise ValueError("the one-body table needs onebody_len entries")
+        col, val = self._outputs(nnz, K, col, val)
+        _ok(lib.cih_ham_fill_onebody(self._h, _ptr(rowptr), K, _ptr(t), _ptr(t1), _ptr(col), _ptr(val),
+                                     _stream(stream)), "ham_fill_onebody")
+        return col[:nnz], val[:, :nnz]
+
     def tbme_index(self, a, b, c, d):
         idx, sg = C.c_int64(), C.c_int32()
         _ok(lib.cih_tbme_index(self._h, a, b, c, d, C.byref(idx), C.byref(sg)), "tbme_index")
@@ -231,6 +275,34 @@ class Basis:
         _ok(lib.cih_ham_fill(self._h, _ptr(rowptr), K, float(hbar_omega), _ptr(t), _ptr(e_sp),
                              _ptr(col), _ptr(val), _stream(stream)), "ham_fill")
         return col[:nnz], val[:, :nnz]
+
+    def fill_rows(self, rowptr, r0: int, r1: int, tbme, hbar_omega: float = 20.0, e_sp=None, stream=None,
+                  nnz_s: int | None = None, col=None, val=None):
+        """Row-sharded fill (cih_ham_fill_rows): rows r0 .. r1 - 1 only, into
+        arrays holding just those rows.  rowptr: the whole row pointers (device);
+        nnz_s = rowptr[r1] - rowptr[r0] (read from the device when not given).
+        Returns (col int32[nnz_s], val float32[K, nnz_s])."""
+        import torch
+        t = self._check_table(tbme)
+        K = t.shape[0]
+        if not (0 <= r0 <= r1 <= self.dim):
+            raise ValueError("row range outside 0 .. dim")
+        if nnz_s is None:
+            nnz_s = int(rowptr[r1].item() - rowptr[r0].item())
+        if col is None:
+            col = torch.empty(nnz_s, dtype=torch.int32, device="cuda")
+        if val is None:
+            val = torch.empty((K, nnz_s), dtype=torch.float32, device="cuda")
+        if (col.dtype != torch.int32 or val.dtype != torch.float32 or not col.is_cuda or not val.is_cuda
+                or col.numel() < nnz_s or val.dim() != 2 or val.shape[0] != K or val.shape[1] != nnz_s
+                or not val.is_contiguous()):
+            raise ValueError("col must hold nnz_s int32 and val be a contiguous (K, nnz_s) float32 CUDA tensor")
+        if e_sp is not None:
+            e_sp = e_sp.to(device="cuda", dtype=torch.float64).contiguous()
+        if nnz_s > 0:
+            _ok(lib.cih_ham_fill_rows(self._h, _ptr(rowptr), r0, r1, K, float(hbar_omega), _ptr(t), _ptr(e_sp),
+                                      _ptr(col), _ptr(val), _stream(stream)), "ham_fill_rows")
+        return col[:nnz_s], val[:, :nnz_s]
 
     def _check_table(self, tbme):
         import torch

@@ -10,6 +10,7 @@
 // bucketed by (2M, parity, N) with a stable counting sort, which yields the
 // (2M, N mod 2, N, bits) order in linear time.
 #include <algorithm>
+#include <tuple>
 #include <memory>
 #include <exception>
 #include <thread>
@@ -374,6 +375,41 @@ int build_pn_split(cih_basis &b)
     return CIH_OK;
 }
 
+// One-body table layout: the combined orbitals stably sorted by (species, 2m,
+// N parity); a run of equal keys is a group.
+void build_onebody_layout(cih_basis &b)
+{
+    OneBodyLayout &L = b.onebody;
+    const int np = b.s[0].n_orb, ntot = np + b.s[1].n_orb;
+    auto key = [&](int a) {
+        const Species &s = b.s[a < np ? 0 : 1];
+        const int k = a < np ? a : a - np;
+        return std::make_tuple(a < np ? 0 : 1, s.om2[k], s.oN[k] & 1);
+    };
+    std::vector<int> ord(ntot);
+    for (int a = 0; a < ntot; ++a) ord[a] = a;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return key(x) < key(y); });
+    L.grp.assign(std::max(ntot, 1), -1);
+    L.loc.assign(std::max(ntot, 1), 0);
+    L.gsize.clear();
+    L.goff.clear();
+    int64_t off = 0;
+    for (int i = 0; i < ntot;) {
+        int j = i;
+        while (j < ntot && key(ord[j]) == key(ord[i])) ++j;
+        const int g = (int)L.gsize.size(), n = j - i;
+        for (int k = i; k < j; ++k) {
+            L.grp[ord[k]] = (int16_t)g;
+            L.loc[ord[k]] = (int16_t)(k - i);
+        }
+        L.gsize.push_back(n);
+        L.goff.push_back((int32_t)off);
+        off += (int64_t)n * (n + 1) / 2;
+        i = j;
+    }
+    L.total = off;
+}
+
 }  // namespace
 
 int build_host_species(const cih_space_t &sp, cih_basis &b)
@@ -480,6 +516,7 @@ int build_host_rest(cih_basis &b)
     if (rc) return rc;
     rc = build_pn_split(b);
     tm.mark("pn split");
+    if (!rc) build_onebody_layout(b);
     return rc;
 }
 

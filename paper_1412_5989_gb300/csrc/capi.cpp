@@ -203,6 +203,29 @@ int cih_tbme_index(cih_basis_h h, int32_t a, int32_t b, int32_t c, int32_t d, in
     return CIH_OK;
 }
 
+int cih_onebody_info(cih_basis_h h, int64_t *len)
+{
+    if (!h || !len) return fail(CIH_ERR_ARG, "NULL argument");
+    *len = h->onebody.total;
+    return CIH_OK;
+}
+
+int cih_onebody_index(cih_basis_h h, int32_t a, int32_t c, int64_t *index)
+{
+    if (!h || !index) return fail(CIH_ERR_ARG, "NULL argument");
+    const int ntot = h->s[0].n_orb + h->s[1].n_orb;
+    *index = -1;
+    if (a < 0 || c < 0 || a >= ntot || c >= ntot) return CIH_OK;
+    const OneBodyLayout &L = h->onebody;
+    const int g = L.grp[a];
+    if (g < 0 || g != L.grp[c]) return CIH_OK;
+    int64_t u = L.loc[a], v = L.loc[c];
+    if (u > v) std::swap(u, v);
+    const int64_t n = L.gsize[g];
+    *index = L.goff[g] + u * n - u * (u - 1) / 2 + (v - u);
+    return CIH_OK;
+}
+
 int cih_basis_destroy(cih_basis_h h)
 {
     if (!h) return fail(CIH_ERR_ARG, "NULL handle");
@@ -242,6 +265,46 @@ int cih_ham_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hba
     if (!tbme_dev && h->layout.total > 0) return fail(CIH_ERR_ARG, "NULL two-body table");
     return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, false, false, e_sp_dev, col_dev, val_dev,
                        (cudaStream_t)stream);
+}
+
+int cih_ham_fill_onebody(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, const float *tbme_dev,
+                         const double *onebody_dev, int32_t *col_dev, float *val_dev, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!rowptr_dev || !col_dev || !val_dev || !onebody_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
+    if (!tbme_dev && h->layout.total > 0) return fail(CIH_ERR_ARG, "NULL two-body table");
+    return launch_fill(*h, rowptr_dev, K, 0.0, tbme_dev, false, false, nullptr, col_dev, val_dev, (cudaStream_t)stream,
+                       0, -1, false, onebody_dev);
+}
+
+int cih_ham_fill_rows(cih_basis_h h, const int64_t *rowptr_dev, int64_t r0, int64_t r1, int32_t K,
+                      double hbar_omega, const float *tbme_dev, const double *e_sp_dev, int32_t *col_dev,
+                      float *val_dev, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (r0 < 0 || r1 < r0 || r1 > h->dim) return fail(CIH_ERR_ARG, "row range outside 0 .. dim");
+    if (r1 == r0) return CIH_OK;
+    if (!rowptr_dev || !col_dev || !val_dev || K < 1) return fail(CIH_ERR_ARG, "NULL array or K < 1");
+    if (!tbme_dev && h->layout.total > 0) return fail(CIH_ERR_ARG, "NULL two-body table");
+    return launch_fill(*h, rowptr_dev, K, hbar_omega, tbme_dev, false, false, e_sp_dev, col_dev, val_dev,
+                       (cudaStream_t)stream, r0, r1, true);
+}
+
+int cih_shard_rows(const int64_t *rowptr_host, int64_t dim, int32_t nshards, int64_t *bounds_host)
+{
+    if (!rowptr_host || !bounds_host || dim < 0 || nshards < 1) return fail(CIH_ERR_ARG, "bad shard arguments");
+    const int64_t nnz = rowptr_host[dim];
+    bounds_host[0] = 0;
+    for (int32_t k = 1; k < nshards; ++k) {
+        // first row whose elements start at or after the k-th equal share of the nonzeros
+        const int64_t target = (int64_t)((__int128)nnz * k / nshards);
+        const int64_t r = std::lower_bound(rowptr_host, rowptr_host + dim, target) - rowptr_host;
+        bounds_host[k] = std::max(bounds_host[k - 1], std::min(r, dim));
+    }
+    bounds_host[nshards] = dim;
+    return CIH_OK;
 }
 
 int cih_ham_fill_interleaved(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, double hbar_omega,

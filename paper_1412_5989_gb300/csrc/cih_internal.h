@@ -91,6 +91,9 @@ struct DevBasis {
     const uint16_t *cself_sfx; // n_p x NL
     const int16_t *self_rel;       // per neutron n: entries of its one-move list below n
     const uint8_t *occ[2];         // per sub-det: its occupied orbitals, ascending (Z_s each)
+    // one-body table layout (see OneBodyLayout)
+    const int16_t *ob_grp, *ob_loc;
+    const int32_t *ob_gsize, *ob_goff;
 };
 
 // pid entry: bits 0..15 local pair index u, bits 16..27 global group id,
@@ -140,6 +143,15 @@ struct Layout {
     std::vector<int32_t> pid;                 // ntot x ntot
 };
 
+// One-body table layout: per species, groups of orbitals with equal (2m, N
+// parity) in the order (species, 2m, parity), members ascending; each group
+// stores its packed upper triangle (a <= c).
+struct OneBodyLayout {
+    int64_t total = 0;
+    std::vector<int16_t> grp, loc;            // per combined orbital: group, place in it
+    std::vector<int32_t> gsize, goff;         // per group
+};
+
 // pn pair index split u(a, b) = S[a][kappa] + r(b): kappa = dense group key
 // ((2m_a + 2m_b + m2span) / 2) * 2 + ((N_a + N_b) & 1), r(b) = number of lower
 // neutron orbitals with the same 2m and N parity as b.  Groups absent from the
@@ -167,6 +179,7 @@ struct cih_basis {
     std::vector<int32_t> nb, nc;
     std::vector<int64_t> rowbase;
     cih::Layout layout;
+    cih::OneBodyLayout onebody;
     cih::PnSplit pn;
     cih::SpeciesBuild sbuild[2]{};
     cih::DevBasis dev{};
@@ -242,8 +255,11 @@ int upload_and_build_neighbours(cih_basis &b, cudaStream_t st, const std::functi
 int launch_count(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
 int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st);
 // interleaved: tables element-major (len x K); em: values element-major (nnz x K)
+// sharded: col / val hold only rows r0 .. r1 - 1 (positions relative to rowptr[r0]);
+// t1: a one-body table (OneBodyLayout) in place of the orbital energies, or null
 int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved, bool em,
-                const double *esp, int32_t *col, float *val, cudaStream_t st, int64_t r0 = 0, int64_t r1 = -1);
+                const double *esp, int32_t *col, float *val, cudaStream_t st, int64_t r0 = 0, int64_t r1 = -1,
+                bool sharded = false, const double *t1 = nullptr);
 int launch_interleave(int K, int64_t len, const float *in, float *out, cudaStream_t st);
 // one-time set-up of the row kernels a call with K sets would launch (shared-
 // memory limits), so that launches made during a stream capture only launch

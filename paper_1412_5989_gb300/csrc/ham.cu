@@ -50,7 +50,37 @@ struct FillArgs {
     const double *esp;        // combined orbital energies or null
     int32_t *col;
     float *val;               // K x nnz
+    int sharded;              // 1: col / val hold only the rows from shard_row on (positions
+    int64_t shard_row;        //    relative to rowptr[shard_row], nnz = that shard's count)
+    const double *t1;         // one-body table (OneBodyLayout) in place of the orbital energies, or null
 };
+
+// table index of t_ac for combined orbitals a, c (either order), -1 if they
+// are not one group of the one-body layout
+__device__ __forceinline__ int onebody_at(const DevBasis &B, int a, int c)
+{
+    const int g = B.ob_grp[a];
+    if (g < 0 || g != B.ob_grp[c]) return -1;
+    int u = B.ob_loc[a], v = B.ob_loc[c];
+    if (u > v) { const int x = u; u = v; v = x; }
+    const int n = B.ob_gsize[g];
+    return B.ob_goff[g] + u * n - ((u * (u - 1)) >> 1) + (v - u);
+}
+
+// t_ac of a one-particle move as a double-float pair (zero without a one-body
+// table); a pair outside the layout is flagged
+__device__ __forceinline__ DF onebody_term(const DevBasis &B, const FillArgs &F, int a, int c, int *status)
+{
+    if (!F.t1) return df_of(0.f);
+    const int k = onebody_at(B, a, c);
+    if (k < 0) {
+        atomicOr(status, 1);
+        return df_of(0.f);
+    }
+    const double t = F.t1[k];
+    const float hi = (float)t;
+    return DF{hi, (float)(t - (double)hi)};
+}
 
 struct GradArgs {
     int K;
@@ -310,8 +340,9 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
             }
             __syncwarp();
             const int eo = w_spos[e];
+            const DF t1v = onebody_term(B, F, a, c, status);      // the one-body term first
             for (int k = lane; k < F.K; k += 32) {
-                DF v = df_of(0.f);
+                DF v = t1v;
                 for (int i = 0; i < sp_n; ++i) {
                     const int2 q = spec[i];
                     if (q.x < 0) continue;
@@ -352,6 +383,8 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
             status[2] = a | (c << 16);
             status[3] = 2 | (kspec << 8);
         }
+        // the one-body term t_ac (one per element: added by its group's first lane)
+        const DF t1v = (MODE == 1 && act && i == 0) ? onebody_term(B, F, a, c, status) : df_of(0.f);
         for (int kk = 0; kk < (MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++kk) {
             if (MODE == 1) {
                 DF v = df_of(0.f);
@@ -359,6 +392,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
                     const float t = __ldg(F.tbme + (int64_t)kk * F.tb_sk + idx * F.tb_si);
                     v = df_of(sg < 0 ? -t : t);
                 }
+                v = df_add(t1v, v);
                 v = warp_sum(v, gsz);
                 if (act && i == 0) {
                     if (kk == 0) R.col[eo] = (int32_t)colj;
@@ -401,7 +435,8 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         if (MODE == 1) {                                   // one-body energies as hi + lo pairs
             float2 *e1w = sptr<float2>(sb, sm::e1);
             for (int a = tid; a < B.ntot && a < kOrbCap; a += kThreads) {
-                const double e = F.esp ? F.esp[a] : F.hw * ((double)B.orbN[a] + 1.5);
+                const int k1 = F.t1 ? onebody_at(B, a, a) : -1;
+                const double e = F.t1 ? (k1 >= 0 ? F.t1[k1] : 0.0) : F.esp ? F.esp[a] : F.hw * ((double)B.orbN[a] + 1.5);
                 const float hi = (float)e;
                 e1w[a] = make_float2(hi, (float)(e - (double)hi));
             }
@@ -415,7 +450,9 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         }
         __syncthreads();
     }
-    const int64_t nnz = MODE == 1 ? rowptr[B.dim] : 0;
+    // stored nonzeros the output arrays hold, and the row pointer of their first element
+    const int64_t sbase = (MODE == 1 && F.sharded) ? rowptr[F.shard_row] : 0;
+    const int64_t nnz = MODE == 1 ? (F.sharded ? rowptr[r1] - sbase : rowptr[B.dim]) : 0;
     const int2 *lg = sptr<int2>(sb, sm::lg);
     unsigned char *wb = sb + sm::warp0 + wid * sm::w_size;
     int4 *w_seg = sptr<int4>(wb, sm::w_seg);
@@ -442,8 +479,8 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         R.ks = (MODE == 1 && F.em) ? 1 : nnz;
         int rowlen = 0;
         if (MODE == 1) {
-            const int64_t r0 = rowptr[row];
-            rowlen = (int)(min(rowptr[row + 1], nnz) - r0);
+            const int64_t r0 = rowptr[row] - sbase;
+            rowlen = (int)(min(rowptr[row + 1] - sbase, nnz) - r0);
             R.col = F.col + r0;
             R.val = F.val + r0 * R.es;
         }
@@ -839,11 +876,12 @@ int launch_scan(const cih_basis &b, int64_t *rowptr, cudaStream_t st)
 }
 
 int launch_fill(const cih_basis &b, const int64_t *rowptr, int K, double hw, const float *tbme, bool interleaved,
-                bool em, const double *esp, int32_t *col, float *val, cudaStream_t st, int64_t r0, int64_t r1)
+                bool em, const double *esp, int32_t *col, float *val, cudaStream_t st, int64_t r0, int64_t r1,
+                bool sharded, const double *t1)
 {
     const int vec4 = interleaved && K % 4 == 0 && ((uintptr_t)tbme & 15) == 0 && (!em || ((uintptr_t)val & 15) == 0);
     FillArgs F{K, hw, tbme, interleaved ? 1 : b.layout.total, interleaved ? (int64_t)K : 1, vec4, em && K > 1 ? 1 : 0,
-               esp, col, val};
+               esp, col, val, sharded ? 1 : 0, r0, t1};
     return launch_rows<1>(b, rowptr, nullptr, F, GradArgs{}, st, false, r0, r1);
 }
 

@@ -917,6 +917,11 @@ int basis_tables_upload(cih_basis &b, cudaStream_t st)
     b.dev.pn_S = d_S; b.dev.pn_gsize = d_gs; b.dev.pn_goff = d_go; b.dev.m2p = d_m2p; b.dev.Np = d_Np;
     b.dev.pn_G = b.pn.G;
     b.dev.pn_m2span = b.pn.m2span;
+    int16_t *d_obg, *d_obl; int32_t *d_obs, *d_obo;
+    if ((rc = upload(b, &d_obg, b.onebody.grp, st)) || (rc = upload(b, &d_obl, b.onebody.loc, st)) ||
+        (rc = upload(b, &d_obs, b.onebody.gsize, st)) || (rc = upload(b, &d_obo, b.onebody.goff, st)))
+        return rc;
+    b.dev.ob_grp = d_obg; b.dev.ob_loc = d_obl; b.dev.ob_gsize = d_obs; b.dev.ob_goff = d_obo;
     return CIH_OK;
 }
 

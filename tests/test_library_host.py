@@ -81,6 +81,21 @@ def test_table_index_matches_oracle(cih, sp):
         assert B.tbme_index(a, b_, c_, d) == S.tbme_index(a, b_, c_, d)
 
 
+@pytest.mark.parametrize("sp", [(3, 3, 2, 0), (2, 1, 3, 1), (4, 4, 4, 0), (1, 0, 3, 1), (0, 2, 2, 0)])
+def test_onebody_layout_matches_oracle(cih, sp):
+    """The library's one-body table layout gives every orbital pair the
+    oracle's index (its own construction: a stable sort by (species, 2m,
+    parity) instead of the oracle's scans)."""
+    B = cih.Basis(*sp, host_only=True)
+    S = oracle.Space(*sp)
+    assert B.onebody_len == S.onebody_len
+    n = sum(B.n_orb)
+    for a in range(n):
+        for c in range(n):
+            assert B.onebody_index(a, c) == S.onebody_index(a, c), (a, c)
+    assert B.onebody_index(-1, 0) == -1 and B.onebody_index(0, n) == -1
+
+
 def test_empty_space(cih):
     B = cih.Basis(2, 2, 2, 1, host_only=True)       # even A, odd 2M
     assert B.dim == 0
