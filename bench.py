@@ -60,6 +60,9 @@ def parse():
                     help="K two-body tables (seeds seed..seed+K-1); K > 1 times the batched fill "
                          "(interleaved tables, element-major values)")
     ap.add_argument("--cpu-rows", type=int, default=60000, help="rows in the oracle's timed sample")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun, every rank builds the whole matrix (default: each rank fills its "
+                         "row shard of about equal nonzeros)")
     return ap.parse_args()
 
 
@@ -229,6 +232,21 @@ def whole_job_rate(world, steps, units_per_step, total_ms):
     return world * steps * units_per_step / (total_ms * 1e-3)
 
 
+def sharded_rate(steps, units_total, total_ms):
+    """Units per second when the ranks split one matrix: each step builds
+    `units_total` units between them; the job takes the slowest rank's time."""
+    return steps * units_total / (total_ms * 1e-3)
+
+
+def rank_rows(rowptr_host, world, rank):
+    """This rank's rows of a row-sharded build: shards of about equal stored
+    nonzeros (cih_shard_rows).  Returns (r0, r1, nonzeros in the shard)."""
+    from paper_1412_5989_gb300 import cih
+    b = cih.shard_bounds(rowptr_host, world)
+    r0, r1 = int(b[rank]), int(b[rank + 1])
+    return r0, r1, int(rowptr_host[r1]) - int(rowptr_host[r0])
+
+
 def side_measurements(args, dev, st, flush, peak, cih, synth, sp, rowptr, col, val, nnz):
     """Measurements beside the headline (not part of `value`): the batched fill
     (4+4 Nmax=4, K=64 tables, element-major values) and Lanczos iterations on
@@ -362,9 +380,14 @@ def run_ours(args, rank, world, local_rank):
     tbme_h = synth.tbme_table(tl, w["seed"])
     tbme = torch.from_numpy(tbme_h).to(dev)
     rowptr, nnz = B0.count()
-    col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    # under torchrun: this rank's row shard (default), or the whole matrix (replicas)
+    sharded = world > 1 and not args.replicas
+    if sharded and K > 1:
+        raise SystemExit("the row-sharded build runs one table (--sets 1)")
+    r0, r1, nnz_s = rank_rows(rowptr.cpu().numpy(), world, rank) if sharded else (0, dim, nnz)
+    col = torch.empty(max(nnz_s, 1), dtype=torch.int32, device=dev)
     if K == 1:
-        val = torch.empty((1, max(nnz, 1)), dtype=torch.float32, device=dev)
+        val = torch.empty((1, max(nnz_s, 1)), dtype=torch.float32, device=dev)
     else:                                                    # K tables, interleaved once (not timed)
         til = cih.tbme_interleave(torch.from_numpy(synth.tbme_tables(tl, range(w["seed"], w["seed"] + K))).to(dev))
         val = torch.empty((max(nnz, 1), K), dtype=torch.float32, device=dev)
@@ -378,7 +401,9 @@ def run_ours(args, rank, world, local_rank):
         ev[1].record(st)
         B.count_into(rowptr)                                 # count + scan
         ev[2].record(st)
-        if K == 1:
+        if sharded:
+            B.fill_rows(rowptr, r0, r1, tbme, nnz_s=nnz_s, col=col, val=val)   # this rank's rows
+        elif K == 1:
             B.fill(rowptr, nnz, tbme, col=col, val=val)      # fill: columns + values
         else:
             B.fill_batched(rowptr, nnz, til, K, col=col, val=val)
@@ -418,7 +443,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms = max_over_ranks(sum(t_step), world, dev)
     if world > 1:
         torch.distributed.barrier()
-    value = whole_job_rate(world, args.steps, nnz, total_ms)
+    value = sharded_rate(args.steps, nnz, total_ms) if sharded else whole_job_rate(world, args.steps, nnz, total_ms)
 
     # gradient / forward time ratio: adjoint over the same structure with a
     # normalised vector, against the fill pass
@@ -441,7 +466,7 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the public API with host buffers
     e2e = None
-    if not args.no_e2e and K == 1:
+    if not args.no_e2e and K == 1 and not sharded:
         # end to end through the library's host-memory call: tables from pinned
         # host memory, the matrix back to pinned host memory, copies inside
         tb_pin = torch.from_numpy(tbme_h).pin_memory()
@@ -469,16 +494,17 @@ def run_ours(args, rank, world, local_rank):
         del col_h, val_h
 
     peak, peak_kind = measured_peak()
-    extra = {} if (args.no_extra or K > 1) else side_measurements(args, dev, st, flush, peak, cih, synth, sp, rowptr, col, val, nnz)
+    extra = {} if (args.no_extra or K > 1 or sharded) else side_measurements(args, dev, st, flush, peak, cih, synth, sp, rowptr, col, val, nnz)
     fill_ms = statistics.median(t_fill)
-    achieved = nnz * bytes_per_nnz / (fill_ms * 1e-3) / 1e9
+    achieved = nnz_s * bytes_per_nnz / (fill_ms * 1e-3) / 1e9
     wpeak = write_only_gbs(dev, st)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "kernel": "k_rows<W,1,K1> (fill)" if K == 1 else f"k_rows<W,1> (batched fill, K={K})",
-                "algorithmic_bytes_per_launch": nnz * bytes_per_nnz,
-                "traffic": fill_traffic(kernel_source_sha()) if (args.workload == "4p4n_nmax6" and K == 1) else None,
+                "algorithmic_bytes_per_launch": nnz_s * bytes_per_nnz,
+                "traffic": fill_traffic(kernel_source_sha()) if (args.workload == "4p4n_nmax6" and K == 1
+                                                                  and not sharded) else None,
                 "write_only_peak": wpeak, "frac_of_write_only": achieved / wpeak,
                 "write_only_source": "float32 fill of a 4 GiB buffer on this GPU, best of 5, CUDA events"}
 
@@ -500,10 +526,12 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(w), "dim": dim, "nnz_half": nnz, "tbme_entries": tl,
                        "tbme_sets": K, "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": (f"row shards of about equal nonzeros over {world} GPUs (basis and "
+                                       f"count on every rank, no collective on the data path)") if sharded
+                       else ("replicas" if world > 1 else "single GPU")},
             "stages_ms": {"basis": statistics.median(t_basis), "count_scan": statistics.median(t_count),
                           "fill": fill_ms, "adjoint": statistics.median(tg)},
             "grad_fwd_ratio": grad_ratio,
