@@ -122,7 +122,7 @@ def kernel_source_sha():
     """Hash of the fill kernel's sources with comments and blank space removed,
     so that only a code change invalidates a recorded capture."""
     h = hashlib.sha256()
-    for f in ("ham.cu", "cih_internal.h"):
+    for f in ("ham.cu", "ham_common.cuh", "cih_internal.h"):
         src = open(os.path.join(ROOT, "paper_1412_5989_gb300", "csrc", f)).read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)

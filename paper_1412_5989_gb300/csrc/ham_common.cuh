@@ -1,6 +1,5 @@
-// Device helpers shared by the row kernels (ham.cu) and the proton-block
-// fill (fill.cu): two-body table lookups and the double-float value sums.
-// Not part of the ABI.
+// Device helpers of the row kernels (ham.cu): two-body table lookups and the
+// double-float value sums.  Not part of the ABI.
 #pragma once
 
 #include <cstdint>
