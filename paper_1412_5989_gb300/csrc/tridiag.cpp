@@ -10,8 +10,8 @@ namespace cih {
 
 // Symmetric tridiagonal eigenproblem (diagonal d, off-diagonal e) by
 // implicit QR steps with Wilkinson shifts, chasing the bulge with Givens
-// rotations.  Each rotation of columns (k, k + 1) is applied to the rows of
-// Z listed in `rows` (all n rows: the eigenvectors; only the last: their last
+// rotations.  Each rotation of columns (k, k + 1) is applied to rows
+// row0..n-1 of Z (row0 = 0: the eigenvectors; row0 = n - 1: only their last
 // components, which is all the Lanczos residual bounds need).  Eigenvalues
 // are returned ascending, Z's columns permuted to match.
 static void qr_sweeps(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &Z, int row0)
