@@ -277,14 +277,15 @@ int cih_autotune_fill(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, doubl
  *   pairs; evals_host: K x nev double (host, ascending; NaN where fewer Ritz
  *   values exist); evec0_dev: NULL or K x dim double (device), the normalised
  *   lowest Ritz vector of each set.
- * Library-allocated for the call: (max_iter + 1) x dim x K double of Lanczos
- * vectors, the transposed index of the strictly-upper part (nnz - dim int64),
- * and for K > 1 an element-major copy of the values (K x nnz float).
- * Deterministic (no atomics in any floating-point sum) as long as no column
- * holds more than 16384 strictly-upper nonzeros; such a column is summed in
- * an order that may vary between runs.  Returns 0, or 1 if
- * some set did not meet tol within max_iter (results still written), or a
- * CIH_ERR_* code. */
+ * The matrix-vector products are those of cih_ham_spmv (each stored nonzero
+ * read once per product, FP32-pair arithmetic, fixed-point mirror sums),
+ * with the bound taken as F (the Lanczos vectors have unit norm); the
+ * orthogonalisation and the vectors stay FP64.
+ * Library-allocated for the call: (max_iter + 2) x dim x K double of Lanczos
+ * vectors and product scratch, dim x K int64 of mirror accumulators, and for
+ * K > 1 an element-major copy of the values (K x nnz float).  Deterministic:
+ * the same inputs give the same bits.  Returns 0, or 1 if some set did not
+ * meet tol within max_iter (results still written), or a CIH_ERR_* code. */
 int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
                        const float *val_dev, int32_t K, int32_t nev, int32_t max_iter,
                        double tol, double *evals_host, double *evec0_dev, void *stream);
@@ -295,6 +296,31 @@ int cih_lanczos_lowest(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *
 int cih_lanczos_lowest_em(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev,
                           const float *val_em_dev, int32_t K, int32_t nev, int32_t max_iter,
                           double tol, double *evals_host, double *evec0_dev, void *stream);
+
+/* y = H x for K matrices sharing one structure, from the stored upper half
+ * (the Lanczos product, Sec. 2): y_i = sum_{j >= i} h_ij x_j + sum_{j < i}
+ * h_ji x_j, each stored nonzero read once.  The GPU's FP64 units are few, so
+ * no FP64 operation runs per nonzero: x is split once into FP32 pairs
+ * hi + lo, a product h (hi + lo) is formed as an FP32 pair (relative error
+ * about 2^-47), and the row part is a double-float sum in an order fixed by
+ * the structure.  Each strictly-upper h_ij x_i goes to column j's
+ * accumulator as a 64-bit fixed-point integer (units 2^-s) by atomic adds,
+ * which commute: the result is deterministic.  The scale keeps every
+ * accumulator below 2^60 through the Cauchy-Schwarz bound
+ * |sum_{i<j} h_ij x_i| <= F ||x||, F the Frobenius norm of the strictly-upper
+ * values of all K sets and ||x|| the largest of the K vector norms; each
+ * mirrored product is rounded to at most one unit 2^-s, about 2^-60 F ||x||.
+ *   val_dev: K x nnz float (set-major) or, when values_em == 1, nnz x K
+ *   (element-major, cih_ham_fill_batched's layout); x_dev, y_dev: dim x K
+ *   double, element-major (x[i * K + s]), distinct arrays; 1 <= K <= 256.
+ * Library-allocated for the call: dim x K int64 accumulators and FP32 pairs,
+ * and for K > 1 set-major values an element-major copy (K x nnz float).  Stream-ordered;
+ * synchronises only to read nnz when that copy is made.  An empty basis
+ * (dim = 0) returns 0 at once, whatever the pointers.  Errors:
+ * CIH_ERR_ARG, CIH_ERR_NOMEM, CIH_ERR_UNSUPPORTED (dim above 2^31),
+ * CIH_ERR_CUDA. */
+int cih_ham_spmv(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev, const float *val_dev,
+                 int32_t K, int32_t values_em, const double *x_dev, double *y_dev, void *stream);
 
 /* Adjoint: d E0 / d t for every two-body table entry t of each of K sets,
  * given the normalised lowest eigenvectors psi (Hellmann-Feynman, E0 =

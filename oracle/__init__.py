@@ -72,6 +72,7 @@ def _load():
     lib.or_count_row_list.argtypes = [P, i64p, C.c_long, i64p]
     lib.or_jacobi.argtypes = [C.c_int, dp, dp, dp]
     lib.or_lanczos.argtypes = [C.c_longlong, i64p, ip, fp, C.c_int, C.c_int, C.c_double, dp, dp, dp, ip]
+    lib.or_half_spmv.argtypes = [C.c_longlong, i64p, ip, fp, dp, dp]
     lib.or_tridiag_eig.restype = C.c_double
     lib.or_tridiag_eig.argtypes = [C.c_int, dp, dp, C.c_int]
     lib.or_grad_elementwise.argtypes = [P, i64p, ip, dp, dp]
@@ -130,6 +131,21 @@ def lanczos(rowptr, col, val, nev=5, max_iter=300, tol=1e-10, v0=None):
     if rc < 0:
         raise ValueError("oracle lanczos: bad arguments")
     return ev, vec, it.value, rc == 0
+
+
+def half_spmv(rowptr, col, val, x):
+    """y = H x for a half-stored CSR matrix (upper triangle with diagonal), FP64."""
+    lib = _load()
+    dim = len(rowptr) - 1
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros(dim)
+    if lib.or_half_spmv(dim, _ptr(rowptr, C.c_longlong), _ptr(col, C.c_int), _ptr(val, C.c_float),
+                        _ptr(x, C.c_double), _ptr(y, C.c_double)) < 0:
+        raise ValueError("oracle half_spmv: bad arguments")
+    return y
 
 
 class Space:

@@ -1099,6 +1099,15 @@ int or_dense_sc(const or_space *S, const float *tbme, const double *esp, double 
 }
 
 /* tridiagonal eigenvalue by bisection, exposed for its own pin */
+/* y = H x for a half-stored matrix (the product Lanczos applies, Sec. 2) */
+int or_half_spmv(long long dim, const long long *rowptr, const int *col, const float *val, const double *x,
+                 double *y)
+{
+    if (dim < 0 || (dim > 0 && (!rowptr || !x || !y))) return -1;
+    half_spmv(dim, rowptr, col, val, x, y);
+    return 0;
+}
+
 double or_tridiag_eig(int m, const double *alpha, const double *beta, int r)
 {
     return tridiag_eig(m, alpha, beta, r);

@@ -62,6 +62,7 @@ _SIGS = {
     "cih_batch_solve": [C.POINTER(Instance), C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int64, _P],
     "cih_lanczos_lowest": [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _P, _P],
     "cih_lanczos_lowest_em": [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _P, _P],
+    "cih_ham_spmv": [_P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P, _P],
     "cih_ham_tbme_grad": [_P, _P, C.c_int32, _P, _P, _P],
     "cih_tridiag_eigen": [C.c_int32, _dp, _dp, _dp, _dp],
     "cih_kernel_launches": [_i64p],
@@ -433,6 +434,21 @@ class Basis:
         rc = _ok(fn(self._h, _ptr(rowptr), _ptr(col), _ptr(v), K, nev, max_iter, tol,
                     ev.ctypes.data_as(_dp), _ptr(vec), _stream(stream)), "lanczos_lowest")
         return ev, vec, rc == 0
+
+    def spmv(self, rowptr, col, val, x, element_major: bool = False, stream=None):
+        """y = H x from the stored upper half (cih_ham_spmv).  val is (K, nnz)
+        set-major or (nnz, K) element-major; x is (dim,) for one set or
+        (dim, K) element-major, float64 CUDA.  Returns y shaped like x."""
+        import torch
+        v = (val if val.dim() == 2 else val.unsqueeze(0)).contiguous()
+        K = v.shape[1] if element_major else v.shape[0]
+        xx = x.to(torch.float64).contiguous()
+        if xx.numel() != self.dim * K or not xx.is_cuda:
+            raise ValueError(f"x must hold dim x K = {self.dim} x {K} float64 values on the GPU")
+        y = torch.empty_like(xx)
+        _ok(lib.cih_ham_spmv(self._h, _ptr(rowptr), _ptr(col), _ptr(v), K, 1 if element_major else 0,
+                             _ptr(xx), _ptr(y), _stream(stream)), "ham_spmv")
+        return y
 
     def tbme_grad(self, rowptr, psi, stream=None):
         """d E0 / d table entry for each set: (K, tbme_len) float64 CUDA tensor."""

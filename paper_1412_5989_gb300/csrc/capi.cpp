@@ -463,6 +463,20 @@ int cih_lanczos_lowest_em(cih_basis_h h, const int64_t *rowptr_dev, const int32_
                          true);
 }
 
+int cih_ham_spmv(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev, const float *val_dev,
+                 int32_t K, int32_t values_em, const double *x_dev, double *y_dev, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (K < 1 || K > 256 || (values_em != 0 && values_em != 1)) return fail(CIH_ERR_ARG, "K or values_em out of range");
+    if (h->dim == 0) return CIH_OK;                               // nothing to multiply
+    if (!rowptr_dev || !col_dev || !val_dev || !x_dev || !y_dev) return fail(CIH_ERR_ARG, "NULL array");
+    if (x_dev == y_dev) return fail(CIH_ERR_ARG, "x and y must not be the same array");
+    return guarded([&]() -> int {
+        return ham_spmv(*h, rowptr_dev, col_dev, val_dev, K, values_em != 0, x_dev, y_dev, (cudaStream_t)stream);
+    });
+}
+
 int cih_ham_tbme_grad(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, const double *psi_dev,
                       double *grad_dev, void *stream)
 {

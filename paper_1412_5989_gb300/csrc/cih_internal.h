@@ -286,6 +286,9 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
             bool values_em = false);
 // device bytes lanczos() allocates for a call
 int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter);
+// y = H x for K sets from the stored upper half (x, y element-major: x[i * K + s])
+int ham_spmv(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val, int K, bool values_em,
+             const double *x, double *y, cudaStream_t st);
 
 // tables from host memory, matrix to host memory, copies overlapped (host_io.cpp)
 int build_host(cih_basis &b, int K, double hw, const float *tbme_h, const double *esp_h, int64_t *rowptr_h,

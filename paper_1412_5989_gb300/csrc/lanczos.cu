@@ -3,10 +3,9 @@
 // structure, all K Krylov sequences advancing together.
 //
 // Device:
-//   - the mirrored half of the symmetric matrix is read through a transposed
-//     index of the strictly-upper part (for each column j, the stored (i, k)
-//     with i < j, sorted by i), so y = H x needs no atomics and is
-//     deterministic;
+//   - y = H x reads each stored nonzero of the upper half once: the row part
+//     in FP64 registers, the mirrored half added to 64-bit fixed-point column
+//     accumulators (integer atomic adds commute, so y is deterministic);
 //   - values element-major (the K values of a nonzero together) and vectors
 //     element-major x[i * K + s], FP64;
 //   - full reorthogonalisation: classical Gram-Schmidt applied twice, dot
@@ -21,6 +20,7 @@
 #include <vector>
 
 #include "cih_internal.h"
+#include "ham_common.cuh"
 
 namespace cih {
 namespace {
@@ -45,74 +45,6 @@ void parallel_sets(int K, F &&fn)
 constexpr int kDotBlocks = 256;
 constexpr int kThreads = 256;
 
-// ---- transposed index of the strictly-upper part
-
-__global__ void k_tcount(int64_t dim, const int64_t *rowptr, const int32_t *col, int32_t *tcnt)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x)
-        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
-            if (col[k] != i) atomicAdd(&tcnt[col[k]], 1);
-}
-
-// entry of stored nonzero k = (i, j), i < j, in column j's list: (i << 32) |
-// low, low = the value's bits when one set (the mirror pass then reads no
-// other array), else k
-__global__ void k_tfill(int64_t dim, const int64_t *rowptr, const int32_t *col, const int64_t *toff, int32_t *tcur,
-                        const float *val1, int64_t *tent)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x)
-        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-            const int32_t j = col[k];
-            if (j == i) continue;
-            const int64_t at = toff[j] + atomicAdd(&tcur[j], 1);
-            const uint32_t low = val1 ? __float_as_uint(val1[k]) : (uint32_t)k;
-            tent[at] = (i << 32) | low;                      // sorts by row first
-        }
-}
-
-// sort each column's entries by row (keys are distinct): bitonic in shared
-// memory, for the columns with lo < length <= TILE
-template <int TILE>
-__global__ void k_tsort(int64_t dim, const int64_t *toff, int64_t *tent, int lo)
-{
-    extern __shared__ int64_t sh[];
-    for (int64_t j = blockIdx.x; j < dim; j += gridDim.x) {
-        const int64_t o = toff[j];
-        const int64_t len64 = toff[j + 1] - o;
-        if (len64 <= lo || len64 > TILE || len64 <= 1) continue;
-        const int len = (int)len64;
-        int P = 1;
-        while (P < len) P <<= 1;
-        for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < len ? tent[o + i] : INT64_MAX;
-        __syncthreads();
-        for (int k = 2; k <= P; k <<= 1)
-            for (int s = k >> 1; s > 0; s >>= 1) {
-                for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                    const int l = i ^ s;
-                    if (l > i) {
-                        const bool up = (i & k) == 0;
-                        const int64_t a = sh[i], c = sh[l];
-                        if ((a > c) == up) { sh[i] = c; sh[l] = a; }
-                    }
-                }
-                __syncthreads();
-            }
-        for (int i = threadIdx.x; i < len; i += blockDim.x) tent[o + i] = sh[i];
-        __syncthreads();
-    }
-}
-constexpr int kTileSmall = 2048, kTileLarge = 16384;   // 16 KB and 128 KB of shared memory
-
-// values of the transposed entries, element-major: vT[t * K + s] = vem[k(t) * K + s]
-__global__ void k_vT(int64_t nt, int K, const int64_t *tent, const float *vem, float *vT)
-{
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nt * K; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = q / K;
-        const int s = (int)(q - t * K);
-        vT[q] = vem[(int64_t)(uint32_t)tent[t] * K + s];
-    }
-}
-
 // element-major values: vem[k * K + s] = val[s * nnz + k]
 __global__ void k_vals_em(int K, int64_t nnz, const float *val, float *vem)
 {
@@ -123,69 +55,184 @@ __global__ void k_vals_em(int K, int64_t nnz, const float *val, float *vem)
     }
 }
 
-// ---- y = H x for K sets.  One warp per row, row part then mirror part.
-// K >= 32: lanes over sets, two sets per lane per pass, nonzeros four at a
-// time; K < 32 (KS = next power of two): 32/KS lane groups split the
-// nonzeros, four per group at a time, then reduce across the groups.  The
-// four independent loads keep more of each row's gathers in flight.  The
-// summation order depends only on the structure.
+// ---- y = H x from the stored upper half, each stored nonzero read once.
+//
+// Row i's warp forms the row part sum_j h_ij x_j in FP64 registers (a fixed
+// order: lanes, then a shuffle tree), and sends each strictly-upper h_ij x_i
+// to column j's accumulator as a 64-bit fixed-point integer (units 2^-s) by
+// an atomic add.  Integer adds commute, so y does not depend on the order in
+// which rows run: the product is deterministic without a transposed copy.
+// k_sym_finish adds the two parts and clears the accumulators.
+//
+// The scale 2^s keeps every accumulator inside 2^60: for column j,
+// |sum_{i<j} h_ij x_i| <= ||h_{.j}|| ||x|| (Cauchy-Schwarz) <= F ||x||, with
+// F the Frobenius norm of the strictly-upper part over all sets, and the
+// Lanczos vectors have ||x|| = 1.  Products are rounded to the nearest unit,
+// so each one carries at most 2^-s-1 of absolute error.
+
+// partial[blk] = this block's sum of the squares of the strictly-upper
+// values of all sets (a warp per row, lanes over (nonzero, set) pairs)
+constexpr int kSumsqThreads = 1024;
+__global__ void __launch_bounds__(kSumsqThreads) k_upper_sumsq(int64_t dim, int K, const int64_t *rowptr,
+                                                               const float *vem, double *partial)
+{
+    __shared__ double red[kSumsqThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid; i < dim; i += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+        const int64_t t1 = rowptr[i + 1] * K;
+        for (int64_t t = (rowptr[i] + 1) * K + lane; t < t1; t += 32) {
+            const double v = vem[t];
+            acc += v * v;
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if (lane == 0) red[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+// sc = (2^s, 2^-s, 2^r, 2^-r) from the sum of squares F^2 (fixed-order sum
+// of the partials) and, when given, the largest squared norm of the K
+// vectors (else the vectors have norm 1), with F ||x|| < 2^e and ||x|| < 2^ex:
+//   s = min(60 - e, 124 - ex): the mirrored products' units 2^-s keep every
+//       accumulator below 2^60, and every x_i 2^s is an FP32 pair;
+//   r = 1 - ex: the row part multiplies x 2^r, of norm below 2 (0 when the
+//       vectors have norm 1).
+__global__ void k_mirror_scale(int parts, const double *partial, int K, const double *xn2, double *sc)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double f2 = 0.0;
+    for (int b = 0; b < parts; ++b) f2 += partial[b];
+    double m = 1.0;
+    if (xn2) {
+        m = 0.0;
+        for (int k = 0; k < K; ++k) m = fmax(m, xn2[k]);
+    }
+    int e = 0, ex = 1;
+    if (f2 > 0.0 && m > 0.0) (void)frexp(sqrt(f2 * m) * (1.0 + 1e-6), &e);
+    if (xn2 && m > 0.0) (void)frexp(sqrt(m) * (1.0 + 1e-6), &ex);
+    const int sh = min(60 - e, 124 - ex), r = xn2 ? 1 - ex : 0;
+    sc[0] = ldexp(1.0, sh);
+    sc[1] = ldexp(1.0, -sh);
+    sc[2] = ldexp(1.0, r);
+    sc[3] = ldexp(1.0, -r);
+}
+
+// The GPU's FP64 units are few, so the product runs in FP32 pairs: x is
+// split once per product into hi + lo floats (xs), a product v (hi + lo) is
+// the pair (v hi, fma(v, hi, -v hi) + v lo) (about 47 bits), row sums are
+// double-float sums, and a mirrored product goes to the fixed-point
+// accumulator as the rounded hi plus the rounded lo (at most 1 unit of
+// error).  No FP64 operation runs per stored nonzero.
+__device__ __forceinline__ float2 split2(double v)
+{
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+__device__ __forceinline__ DF df_prod(float v, float2 x)
+{
+    const float p = v * x.x;
+    return DF{p, fmaf(v, x.y, fmaf(v, x.x, -p))};
+}
+
+// f rounded to the nearest integer (halves away from zero) by integer
+// operations on its bits; |f| < 2^62.  (The hardware's 64-bit conversions run
+// on the FP64 units.)
+__device__ __forceinline__ long long round_ll(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const int sh = (int)((b >> 23) & 0xFFu) - 150;                 // |f| = m 2^sh
+    const unsigned m = (b & 0x7FFFFFu) | 0x800000u;
+    long long v = 0;                                                // |f| < 0.5, zero, subnormal
+    if (sh >= 0) v = (long long)m << sh;
+    else if (sh >= -24) v = (long long)((m + (1u << (-sh - 1))) >> -sh);
+    return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ void mirror_add(unsigned long long *a, DF q)
+{
+    atomicAdd(a, (unsigned long long)(round_ll(q.hi) + round_ll(q.lo)));
+}
+
+// xs[t] = x[t] 2^r (the row part's factor) and xm[t] = x[t] 2^s (the
+// mirrored products'), each as hi + lo floats
+__global__ void k_split(int64_t n, const double *x, const double *sc, float2 *xs, float2 *xm)
+{
+    const double fr = sc[2], fs = sc[0];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[t];
+        xs[t] = split2(v * fr);
+        xm[t] = split2(v * fs);
+    }
+}
+
+// K >= 32: lanes over sets, two per lane per pass; K < 32 (KS = next power
+// of two): 32/KS lane groups split the row's nonzeros, four at a time per
+// group, and the groups' row sums are reduced at the end.  Each block walks
+// one contiguous run of rows, so that rows of one proton sub-determinant
+// (which touch the same x and accumulator blocks) share its L1.
 template <int KS>
-__global__ void k_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t *col, const int64_t *toff,
-                       const int64_t *tent, const float *vem, const float *vT, const double *x, double *y)
+__global__ void __launch_bounds__(kThreads, 4) k_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t *col, const float *vem,
+                       const float2 *xs, const float2 *xm, float2 *yrow, unsigned long long *yfix)
 {
     const int lane = threadIdx.x & 31;
-    // each block walks one contiguous run of rows, so that rows of the same
-    // proton sub-determinant (which gather the same x blocks) share its L1
     const int64_t per = (dim + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * per, r1 = min(dim, r0 + per);
     const int wpb = blockDim.x >> 5;
     for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += wpb) {
-        const int64_t a0 = rowptr[i], a1 = rowptr[i + 1], b0 = toff[i], b1 = toff[i + 1];
+        const int64_t a0 = rowptr[i], a1 = rowptr[i + 1];
         if (KS >= 32) {
             for (int s0 = 0; s0 < K; s0 += 64) {
                 const int sa = s0 + lane, sb = s0 + 32 + lane;
                 const bool ha = sa < K, hb = sb < K;
-                double acc_a = 0.0, acc_b = 0.0;
+                const float2 Xa = ha ? xm[i * K + sa] : make_float2(0.f, 0.f);
+                const float2 Xb = hb ? xm[i * K + sb] : make_float2(0.f, 0.f);
+                DF acc_a = df_of(0.f), acc_b = df_of(0.f);
                 int64_t k = a0;
                 for (; k + 3 < a1; k += 4) {
                     int64_t c[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) c[u] = (int64_t)col[k + u] * K;
+                    float va[4], vb[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        if (ha) acc_a += (double)vem[(k + u) * K + sa] * __ldg(x + c[u] + sa);
-                        if (hb) acc_b += (double)vem[(k + u) * K + sb] * __ldg(x + c[u] + sb);
+                        c[u] = col[k + u];
+                        va[u] = ha ? vem[(k + u) * K + sa] : 0.f;
+                        vb[u] = hb ? vem[(k + u) * K + sb] : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (ha) acc_a = df_add(acc_a, df_prod(va[u], xs[c[u] * K + sa]));
+                        if (hb) acc_b = df_add(acc_b, df_prod(vb[u], xs[c[u] * K + sb]));
+                        if (c[u] != i) {
+                            if (ha) mirror_add(yfix + c[u] * K + sa, df_prod(va[u], Xa));
+                            if (hb) mirror_add(yfix + c[u] * K + sb, df_prod(vb[u], Xb));
+                        }
                     }
                 }
                 for (; k < a1; ++k) {
-                    const int64_t c = (int64_t)col[k] * K;
-                    if (ha) acc_a += (double)vem[k * K + sa] * __ldg(x + c + sa);
-                    if (hb) acc_b += (double)vem[k * K + sb] * __ldg(x + c + sb);
-                }
-                int64_t t = b0;
-                for (; t + 3 < b1; t += 4) {
-                    int64_t r[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) r[u] = (tent[t + u] >> 32) * K;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (ha) acc_a += (double)vT[(t + u) * K + sa] * __ldg(x + r[u] + sa);
-                        if (hb) acc_b += (double)vT[(t + u) * K + sb] * __ldg(x + r[u] + sb);
+                    const int64_t c = col[k];
+                    const float va = ha ? vem[k * K + sa] : 0.f, vb = hb ? vem[k * K + sb] : 0.f;
+                    if (ha) acc_a = df_add(acc_a, df_prod(va, xs[c * K + sa]));
+                    if (hb) acc_b = df_add(acc_b, df_prod(vb, xs[c * K + sb]));
+                    if (c != i) {
+                        if (ha) mirror_add(yfix + c * K + sa, df_prod(va, Xa));
+                        if (hb) mirror_add(yfix + c * K + sb, df_prod(vb, Xb));
                     }
                 }
-                for (; t < b1; ++t) {
-                    const int64_t r = (tent[t] >> 32) * K;
-                    if (ha) acc_a += (double)vT[t * K + sa] * __ldg(x + r + sa);
-                    if (hb) acc_b += (double)vT[t * K + sb] * __ldg(x + r + sb);
-                }
-                if (ha) y[i * K + sa] = acc_a;
-                if (hb) y[i * K + sb] = acc_b;
+                if (ha) yrow[i * K + sa] = make_float2(acc_a.hi, acc_a.lo);
+                if (hb) yrow[i * K + sb] = make_float2(acc_b.hi, acc_b.lo);
             }
         } else {
             constexpr int G = 32 / KS;
             const int g = lane / KS, s = lane % KS;
-            double acc = 0.0;
+            DF acc = df_of(0.f);
             if (s < K) {
+                const float2 Xi = xm[i * K + s];
                 int64_t k = a0 + g;
                 for (; k + 3 * G < a1; k += 4 * G) {
                     int64_t c[4];
@@ -195,30 +242,40 @@ __global__ void k_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t 
                         c[u] = col[k + u * G];
                         v[u] = vem[(k + u * G) * K + s];
                     }
+                    float2 xj[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) acc += (double)v[u] * __ldg(x + c[u] * K + s);
-                }
-                for (; k < a1; k += G) acc += (double)vem[k * K + s] * __ldg(x + (int64_t)col[k] * K + s);
-                int64_t t = b0 + g;
-                for (; t + 3 * G < b1; t += 4 * G) {
-                    int64_t e[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) e[u] = tent[t + u * G];
+                    for (int u = 0; u < 4; ++u) xj[u] = xs[c[u] * K + s];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float v = KS == 1 ? __uint_as_float((uint32_t)e[u]) : vT[(t + u * G) * K + s];
-                        acc += (double)v * __ldg(x + (e[u] >> 32) * K + s);
+                        acc = df_add(acc, df_prod(v[u], xj[u]));
+                        if (c[u] != i) mirror_add(yfix + c[u] * K + s, df_prod(v[u], Xi));
                     }
                 }
-                for (; t < b1; t += G) {
-                    const int64_t e = tent[t];
-                    const float v = KS == 1 ? __uint_as_float((uint32_t)e) : vT[t * K + s];
-                    acc += (double)v * __ldg(x + (e >> 32) * K + s);
+                for (; k < a1; k += G) {
+                    const int64_t c = col[k];
+                    const float v = vem[k * K + s];
+                    acc = df_add(acc, df_prod(v, xs[c * K + s]));
+                    if (c != i) mirror_add(yfix + c * K + s, df_prod(v, Xi));
                 }
             }
-            for (int d = 16; d >= KS; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
-            if (g == 0 && s < K) y[i * K + s] = acc;
+            for (int d = 16; d >= KS; d >>= 1) {
+                const DF o{__shfl_xor_sync(0xffffffffu, acc.hi, d), __shfl_xor_sync(0xffffffffu, acc.lo, d)};
+                acc = df_add(acc, o);
+            }
+            if (g == 0 && s < K) yrow[i * K + s] = make_float2(acc.hi, acc.lo);
         }
+    }
+}
+
+// y[t] = row part 2^-r + mirrored part 2^-s; the accumulators are cleared
+// for the next product
+__global__ void k_sym_finish(int64_t n, const double *sc, const float2 *yrow, double *y, unsigned long long *yfix)
+{
+    const double sinv = sc[1], rinv = sc[3];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const float2 r = yrow[t];
+        y[t] = ((double)r.x + (double)r.y) * rinv + (double)(long long)yfix[t] * sinv;
+        yfix[t] = 0ull;
     }
 }
 
@@ -326,11 +383,10 @@ int grid_for(int64_t n)
 int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter)
 {
     const int64_t m = std::min<int64_t>(max_iter, dim);
-    const int64_t nt = std::max<int64_t>(nnz - dim, 1);
-    int64_t bytes = 4 * (dim + 1) + 8 * (dim + 1) + 8 * nt;          // transposed index
-    bytes += 8 * (m + 1) * dim * K + 8 * dim * K;                   // Lanczos vectors, w
-    bytes += 8 * (m + 1) * K * kDotBlocks + 8 * (m + 1) * K + 8 * K; // dot partials, h, scale
-    if (K > 1) bytes += 4 * nnz * K + 4 * nt * K;                   // element-major values, mirror values
+    int64_t bytes = 8 * (m + 1) * dim * K + 8 * dim * K;            // Lanczos vectors, w
+    bytes += 32 * dim * K;                                          // mirror accumulators, split x, row part
+    bytes += 8 * (m + 1) * K * kDotBlocks + 8 * (m + 1) * K + 8 * K + 32; // dot partials, h, scale
+    if (K > 1) bytes += 4 * nnz * K;                                // element-major values
     return bytes + 8 * 256;                                         // allocation granules
 }
 
@@ -358,70 +414,48 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
         bufs.push_back(*p);
         return true;
     };
-    int32_t *tcnt = nullptr;
-    int64_t *toff = nullptr, *tent = nullptr;
-    float *vem = nullptr, *vT = nullptr;
-    double *V = nullptr, *w = nullptr, *partial = nullptr, *hdev = nullptr, *fdev = nullptr;
-    const int64_t nt = std::max<int64_t>(nnz - dim, 1);             // strictly upper entries
-    bool ok = alloc((void **)&tcnt, sizeof(int32_t) * (dim + 1)) && alloc((void **)&toff, sizeof(int64_t) * (dim + 1)) &&
-              alloc((void **)&tent, sizeof(int64_t) * nt) &&
+    float *vem = nullptr;
+    unsigned long long *yfix = nullptr;
+    float2 *xs = nullptr, *xm = nullptr, *yrow = nullptr;
+    double *V = nullptr, *w = nullptr, *partial = nullptr, *hdev = nullptr, *fdev = nullptr, *sc = nullptr;
+    bool ok = alloc((void **)&yfix, sizeof(unsigned long long) * (size_t)vstride) &&
+              alloc((void **)&xs, sizeof(float2) * (size_t)vstride) &&
+              alloc((void **)&xm, sizeof(float2) * (size_t)vstride) &&
+              alloc((void **)&yrow, sizeof(float2) * (size_t)vstride) &&
               alloc((void **)&V, sizeof(double) * (size_t)(m_max + 1) * vstride) &&
               alloc((void **)&w, sizeof(double) * vstride) &&
               alloc((void **)&partial, sizeof(double) * (size_t)(m_max + 1) * K * kDotBlocks) &&
-              alloc((void **)&hdev, sizeof(double) * (size_t)(m_max + 1) * K) && alloc((void **)&fdev, sizeof(double) * K);
+              alloc((void **)&hdev, sizeof(double) * (size_t)(m_max + 1) * K) && alloc((void **)&fdev, sizeof(double) * K) &&
+              alloc((void **)&sc, sizeof(double) * 4);
     if (ok && K > 1 && !values_em) ok = alloc((void **)&vem, sizeof(float) * (size_t)nnz * K);
-    if (ok && K > 1) ok = alloc((void **)&vT, sizeof(float) * (size_t)nt * K);
     int rc = ok ? CIH_OK : fail(CIH_ERR_NOMEM, "lanczos: device memory");
     const int g = grid_for(vstride);
     const int gr = (int)std::min<int64_t>((dim + 7) / 8, 152 * 32);
 
-    // transposed index (built once for all sets)
+    // element-major values, the mirror scale and cleared accumulators (no host synchronisation)
     if (!rc) {
-        cudaMemsetAsync(tcnt, 0, sizeof(int32_t) * (dim + 1), st);
-        count_launches(1);
-        k_tcount<<<grid_for(dim), kThreads, 0, st>>>(dim, rowptr, col, tcnt);
-        std::vector<int32_t> hc(dim);
-        e = cudaMemcpyAsync(hc.data(), tcnt, sizeof(int32_t) * dim, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "lanczos: transpose count");
-        if (!rc) {
-            std::vector<int64_t> ho(dim + 1, 0);
-            for (int64_t j = 0; j < dim; ++j) ho[j + 1] = ho[j] + hc[j];
-            cudaMemcpyAsync(toff, ho.data(), sizeof(int64_t) * (dim + 1), cudaMemcpyHostToDevice, st);
-            cudaMemsetAsync(tcnt, 0, sizeof(int32_t) * (dim + 1), st);
+        if (K > 1 && !values_em) {
             count_launches(1);
-            k_tfill<<<grid_for(dim), kThreads, 0, st>>>(dim, rowptr, col, toff, tcnt, K == 1 ? val : nullptr, tent);
-            // columns up to 2048 entries, then the longer ones (up to 16384) one per SM;
-            // longer columns keep the fill order, which may vary from run to run
-            const int gs = (int)std::min<int64_t>(dim, 65535);
-            count_launches(2);
-            k_tsort<kTileSmall><<<gs, 256, kTileSmall * sizeof(int64_t), st>>>(dim, toff, tent, 1);
-            cudaFuncSetAttribute(k_tsort<kTileLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kTileLarge * (int)sizeof(int64_t));
-            k_tsort<kTileLarge><<<152, 1024, kTileLarge * sizeof(int64_t), st>>>(dim, toff, tent, kTileSmall);
-            if (K > 1 && !values_em) {
-                count_launches(1);
-                k_vals_em<<<grid_for(nnz * K), kThreads, 0, st>>>(K, nnz, val, vem);
-            } else {
-                vem = const_cast<float *>(val);                     // already element-major
-            }
-            if (K > 1 && nnz > dim) {                               // mirror values in column order
-                count_launches(1);
-                k_vT<<<grid_for((nnz - dim) * K), kThreads, 0, st>>>(nnz - dim, K, tent, vem, vT);
-            }
-            e = cudaStreamSynchronize(st);                          // the host offsets go out of scope here
-            if (e != cudaSuccess) rc = cuda_fail(e, "lanczos: transpose");
+            k_vals_em<<<grid_for(nnz * K), kThreads, 0, st>>>(K, nnz, val, vem);
+        } else {
+            vem = const_cast<float *>(val);                         // K = 1, or already element-major
         }
+        cudaMemsetAsync(yfix, 0, sizeof(unsigned long long) * (size_t)vstride, st);
+        count_launches(2);
+        k_upper_sumsq<<<kDotBlocks, kSumsqThreads, 0, st>>>(dim, K, rowptr, vem, partial);
+        k_mirror_scale<<<1, 32, 0, st>>>(kDotBlocks, partial, K, nullptr, sc);
     }
 
     auto spmv = [&](const double *x, double *y) {
-        count_launches(1);
-        if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
-        else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
-        else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
-        else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
-        else if (K <= 8) k_spmv<8><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
-        else k_spmv<16><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, toff, tent, vem, vT, x, y);
+        count_launches(3);
+        k_split<<<g, kThreads, 0, st>>>(vstride, x, sc, xs, xm);
+        if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else if (K <= 8) k_spmv<8><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else k_spmv<16><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        k_sym_finish<<<g, kThreads, 0, st>>>(vstride, sc, yrow, y, yfix);
     };
     // h[r][s] = V[r] . w for r < nvec: into hdev (device) and hh (host)
     std::vector<double> hh((size_t)(m_max + 1) * K);
@@ -525,6 +559,71 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
     }
     cudaMemPoolTrimTo(b.pool, 0);                            // the Lanczos vectors go back to the system
     return rc ? rc : not_converged;
+}
+
+
+int ham_spmv(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val, int K, bool values_em,
+             const double *x, double *y, cudaStream_t st)
+{
+    const int64_t dim = b.dim;
+    if (dim == 0) return CIH_OK;
+    if (K > kThreads) return fail(CIH_ERR_UNSUPPORTED, "spmv: at most 256 sets per call");
+    if (dim > INT32_MAX) return fail(CIH_ERR_UNSUPPORTED, "spmv: dimension above 2^31");
+    int64_t nnz = 0;
+    if (K > 1 && !values_em) {
+        cudaError_t e = cudaMemcpyAsync(&nnz, rowptr + dim, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "spmv: read nnz");
+    }
+    const int64_t n = dim * K;
+    std::vector<void *> bufs;
+    auto alloc = [&](void **p, size_t bytes) -> bool {
+        if (cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), b.pool, st) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        bufs.push_back(*p);
+        return true;
+    };
+    unsigned long long *yfix = nullptr;
+    float2 *xs = nullptr, *xm = nullptr, *yrow = nullptr;
+    double *partial = nullptr, *xpart = nullptr, *xn2 = nullptr, *sc = nullptr;
+    float *vem = nullptr;
+    bool ok = alloc((void **)&yfix, sizeof(unsigned long long) * (size_t)n) &&
+              alloc((void **)&xs, sizeof(float2) * (size_t)n) && alloc((void **)&xm, sizeof(float2) * (size_t)n) &&
+              alloc((void **)&yrow, sizeof(float2) * (size_t)n) &&
+              alloc((void **)&partial, sizeof(double) * kDotBlocks) &&
+              alloc((void **)&xpart, sizeof(double) * (size_t)K * kDotBlocks) &&
+              alloc((void **)&xn2, sizeof(double) * K) && alloc((void **)&sc, sizeof(double) * 4);
+    if (ok && K > 1 && !values_em) ok = alloc((void **)&vem, sizeof(float) * (size_t)nnz * K);
+    int rc = ok ? CIH_OK : fail(CIH_ERR_NOMEM, "spmv: device memory");
+    if (!rc) {
+        if (K > 1 && !values_em) {
+            count_launches(1);
+            k_vals_em<<<grid_for(nnz * K), kThreads, 0, st>>>(K, nnz, val, vem);
+        } else {
+            vem = const_cast<float *>(val);
+        }
+        cudaMemsetAsync(yfix, 0, sizeof(unsigned long long) * (size_t)n, st);
+        count_launches(7);
+        k_upper_sumsq<<<kDotBlocks, kSumsqThreads, 0, st>>>(dim, K, rowptr, vem, partial);
+        k_dots<<<dim3(kDotBlocks, 1), kThreads, 0, st>>>(dim, K, 1, x, n, x, xpart);
+        k_dots_finish<<<(K + 255) / 256, 256, 0, st>>>(K, kDotBlocks, xpart, xn2);
+        k_mirror_scale<<<1, 32, 0, st>>>(kDotBlocks, partial, K, xn2, sc);
+        k_split<<<grid_for(n), kThreads, 0, st>>>(n, x, sc, xs, xm);
+        const int gr = (int)std::min<int64_t>((dim + 7) / 8, 152 * 32);
+        if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else if (K <= 8) k_spmv<8><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        else k_spmv<16><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+        k_sym_finish<<<grid_for(n), kThreads, 0, st>>>(n, sc, yrow, y, yfix);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "spmv kernels");
+    }
+    for (void *p : bufs) cudaFreeAsync(p, st);
+    return rc;
 }
 
 }  // namespace cih

@@ -153,6 +153,8 @@ def test_entry_points_reject_bad_arguments_without_a_gpu(cih):
     ev = (C.c_double * 4)()
     assert lib.cih_lanczos_lowest_em(h, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), 1, 1, 10, 1e-8, ev,
                                      None, None) == -1
+    assert lib.cih_ham_spmv(h, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), 1, 0, C.c_void_p(16),
+                            C.c_void_p(24), None) == -1
     w, c, ms = C.c_int32(), C.c_int32(), C.c_float()
     assert lib.cih_autotune_fill(h, C.c_void_p(16), 1, 20.0, C.c_void_p(16), 0, None, C.c_void_p(16),
                                  C.c_void_p(16), None, C.byref(w), C.byref(c), C.byref(ms)) == -1

@@ -381,6 +381,22 @@ def test_lanczos_matches_dense():
     assert np.linalg.norm(H @ vec - ev[0] * vec) <= 1e-8 * np.abs(w).max()
 
 
+@pytest.mark.parametrize("sp", [(3, 3, 2, 0), (2, 1, 3, 1), (1, 0, 3, 1)])
+def test_half_spmv_equals_the_dense_product(sp):
+    """The half-stored product (upper triangle with diagonal, mirrored on the
+    fly) against the dense Slater-Condon matrix times x: a dropped mirror term,
+    a doubled diagonal or a transposed access fails it."""
+    S = oracle.Space(*sp)
+    t = synth.tbme_table(S.tbme_len, 4)
+    rp, col, val = S.half_csr(t)
+    x = np.random.default_rng(1).standard_normal(S.dim)
+    H = S.dense_sc(t)
+    want = dense_from_half(rp, col, val) @ x
+    got = oracle.half_spmv(rp, col, val, x)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+    np.testing.assert_allclose(got, H @ x, rtol=0, atol=1e-5 * np.abs(H).sum(axis=1).max() * np.abs(x).max())
+
+
 def test_lanczos_degenerate_spectrum_gives_distinct_values():
     S = oracle.Space(3, 3, 2, 0)
     rp, col, val = S.half_csr(np.zeros(S.tbme_len, np.float32))
