@@ -149,12 +149,6 @@ inline size_t smem_bytes(int nS) { return (size_t)sm::S<WARPS> + ((size_t)nS * 2
 template <class T>
 __device__ __forceinline__ T *sptr(unsigned char *base, int off) { return reinterpret_cast<T *>(base + off); }
 
-__device__ __forceinline__ double warp_sum(double v, int width)
-{
-    for (int d = width >> 1; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d, width);
-    return v;
-}
-
 __device__ __forceinline__ DF warp_sum(DF v, int width)
 {
     for (int d = width >> 1; d > 0; d >>= 1) {
@@ -263,21 +257,35 @@ __device__ __forceinline__ void put_values_coop(const FillArgs &F, const RowOut 
     const int L = F.K >> 2;                                      // float4s per element
     const int last = 31 - __clz(am);
     if (L <= 32) {
+        // four rounds of P elements at a time: the four table reads are in
+        // flight together before their stores
+        constexpr int kB = 4;
         const int P = 32 / L, sub = lane / L, q = lane % L;
-        for (int j0 = 0; j0 <= last; j0 += P) {
-            const int src = j0 + sub;
-            const int jidx = __shfl_sync(0xffffffffu, idx, src & 31);
-            const int je = __shfl_sync(0xffffffffu, e, src & 31);
-            const int js = __shfl_sync(0xffffffffu, sgn, src & 31);
-            if (src < 32 && ((am >> src) & 1)) {
-                const int sm = js ? (int)0x80000000 : 0;
-                float4 v = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)jidx * F.K) + q);
-                v.x = __int_as_float(__float_as_int(v.x) ^ sm);
-                v.y = __int_as_float(__float_as_int(v.y) ^ sm);
-                v.z = __int_as_float(__float_as_int(v.z) ^ sm);
-                v.w = __int_as_float(__float_as_int(v.w) ^ sm);
-                reinterpret_cast<float4 *>(R.val + (int64_t)je * R.es)[q] = v;
+        for (int j0 = 0; j0 <= last; j0 += kB * P) {
+            float4 v[kB];
+            int64_t at[kB];
+            bool on[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int src = j0 + u * P + sub;
+                const int jidx = __shfl_sync(0xffffffffu, idx, src & 31);
+                const int je = __shfl_sync(0xffffffffu, e, src & 31);
+                const int js = __shfl_sync(0xffffffffu, sgn, src & 31);
+                on[u] = src < 32 && ((am >> (src & 31)) & 1);
+                at[u] = (int64_t)je * R.es;
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (on[u]) {
+                    const int sm = js ? (int)0x80000000 : 0;
+                    v[u] = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)jidx * F.K) + q);
+                    v[u].x = __int_as_float(__float_as_int(v[u].x) ^ sm);
+                    v[u].y = __int_as_float(__float_as_int(v[u].y) ^ sm);
+                    v[u].z = __int_as_float(__float_as_int(v[u].z) ^ sm);
+                    v[u].w = __int_as_float(__float_as_int(v[u].w) ^ sm);
+                }
             }
+#pragma unroll
+            for (int u = 0; u < kB; ++u)                          // evict-first: the tables stay in L2
+                if (on[u]) __stcs(reinterpret_cast<float4 *>(R.val + at[u]) + q, v[u]);
         }
     } else {
         for (int j = 0; j <= last; ++j) {
@@ -317,42 +325,57 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
     const int ns = nslow;
     const int sp_n = A - 1;
     if (MODE == 1 && !K1 && F.K >= kLaneSets) {
-        // K sets: one element at a time; lanes over spectators find the table
-        // entries, then lanes over sets sum them in spectator order
+        // K sets: the table entries of 32 / (A - 1) elements at a time (lanes
+        // over (element, spectator) pairs, so their lookups run together), then
+        // per element lanes over sets sum them in spectator order
         int2 *spec = reinterpret_cast<int2 *>(const_cast<int16_t *>(w_occ) + kMaxA);
-        for (int e = 0; e < ns; ++e) {
-            const uint32_t code = w_scode[e];
-            const int base = (code >> 31) ? nbase : 0;
-            const int a = base + (int)(code & 0xFF), c = base + (int)((code >> 8) & 0xFF);
-            const int sgn = (code >> 16) & 1;
-            int ia = 0;
-            for (int x = 0; x < A; ++x) ia += (w_occ[x] < a);
-            if (lane < sp_n) {
-                const int kspec = w_occ[lane + (lane >= ia ? 1 : 0)];
-                int64_t idx = 0;
-                int sg = 1;
-                const bool ok = tbme_at(B, lg, a, kspec, c, kspec, idx, sg);
-                if (!ok && atomicOr(status, 1) == 0) {
-                    status[2] = a | (c << 16);
-                    status[3] = 2 | (kspec << 8);
+        const int per = sp_n > 0 ? 32 / sp_n : 32;
+        for (int e0 = 0; e0 < ns; e0 += per) {
+            {
+                const int ei = sp_n > 0 ? lane / sp_n : lane, i = sp_n > 0 ? lane % sp_n : 0;
+                const int e = e0 + ei;
+                if (ei < per && e < ns && i < sp_n) {
+                    const uint32_t code = w_scode[e];
+                    const int base = (code >> 31) ? nbase : 0;
+                    const int a = base + (int)(code & 0xFF), c = base + (int)((code >> 8) & 0xFF);
+                    int ia = 0;
+                    for (int x = 0; x < A; ++x) ia += (w_occ[x] < a);
+                    const int kspec = w_occ[i + (i >= ia ? 1 : 0)];
+                    int64_t idx = 0;
+                    int sg = 1;
+                    const bool ok = tbme_at(B, lg, a, kspec, c, kspec, idx, sg);
+                    if (!ok && atomicOr(status, 1) == 0) {
+                        status[2] = a | (c << 16);
+                        status[3] = 2 | (kspec << 8);
+                    }
+                    spec[ei * sp_n + i] = make_int2(ok ? (int)idx : -1, sg);
                 }
-                spec[lane] = make_int2(ok ? (int)idx : -1, sg);
             }
             __syncwarp();
-            const int eo = w_spos[e];
-            const DF t1v = onebody_term(B, F, a, c, status);      // the one-body term first
-            for (int k = lane; k < F.K; k += 32) {
-                DF v = t1v;
-                for (int i = 0; i < sp_n; ++i) {
-                    const int2 q = spec[i];
-                    if (q.x < 0) continue;
-                    const float t = __ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)q.x * F.tb_si);
-                    v = df_add(v, df_of(q.y < 0 ? -t : t));
+            const int ne = min(per, ns - e0);
+            for (int j = 0; j < ne; ++j) {
+                const int e = e0 + j;
+                const uint32_t code = w_scode[e];
+                const int base = (code >> 31) ? nbase : 0;
+                const int a = base + (int)(code & 0xFF), c = base + (int)((code >> 8) & 0xFF);
+                const int sgn = (code >> 16) & 1;
+                const int eo = w_spos[e];
+                const DF t1v = onebody_term(B, F, a, c, status);      // the one-body term first
+                const int2 *sj = spec + j * sp_n;
+                for (int k = lane; k < F.K; k += 32) {
+                    DF v = t1v;
+#pragma unroll 8
+                    for (int i = 0; i < sp_n; ++i) {
+                        const int2 q = sj[i];
+                        if (q.x < 0) continue;
+                        const float t = __ldg(F.tbme + (int64_t)k * F.tb_sk + (int64_t)q.x * F.tb_si);
+                        v = df_add(v, df_of(q.y < 0 ? -t : t));
+                    }
+                    const float r = df_round(v);
+                    R.val[(int64_t)eo * R.es + (int64_t)k * R.ks] = sgn ? -r : r;
                 }
-                const float r = df_round(v);
-                R.val[(int64_t)eo * R.es + (int64_t)k * R.ks] = sgn ? -r : r;
+                if (lane == 0) R.col[eo] = w_scol[e];
             }
-            if (lane == 0) R.col[eo] = w_scol[e];
             __syncwarp();
         }
         nslow = 0;
@@ -515,6 +538,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 }
                 for (int k = lane; k < F.K; k += 32) {
                     DF acc = df_of(0.f);
+#pragma unroll 4
                     for (int l = 0; l < npairs; ++l) {
                         const int32_t idx = w_scol[l];
                         if (idx < 0) continue;

@@ -71,23 +71,29 @@ __global__ void k_vals_em(int K, int64_t nnz, const float *val, float *vem)
 // so each one carries at most 2^-s-1 of absolute error.
 
 // partial[blk] = this block's sum of the squares of the strictly-upper
-// values of all sets (a warp per row, lanes over (nonzero, set) pairs)
+// values of all sets (a warp per row, lanes over (nonzero, set) pairs), in
+// double-float sums of the exact FP32-pair squares
 constexpr int kSumsqThreads = 1024;
 __global__ void __launch_bounds__(kSumsqThreads) k_upper_sumsq(int64_t dim, int K, const int64_t *rowptr,
                                                                const float *vem, double *partial)
 {
     __shared__ double red[kSumsqThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double acc = 0.0;
+    DF acc = df_of(0.f);
     for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid; i < dim; i += (int64_t)gridDim.x * (blockDim.x >> 5)) {
         const int64_t t1 = rowptr[i + 1] * K;
+#pragma unroll 4
         for (int64_t t = (rowptr[i] + 1) * K + lane; t < t1; t += 32) {
-            const double v = vem[t];
-            acc += v * v;
+            const float v = vem[t];
+            const float p = v * v;
+            acc = df_add(acc, DF{p, fmaf(v, v, -p)});
         }
     }
-    for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
-    if (lane == 0) red[wid] = acc;
+    for (int d = 16; d > 0; d >>= 1) {
+        const DF o{__shfl_xor_sync(0xffffffffu, acc.hi, d), __shfl_xor_sync(0xffffffffu, acc.lo, d)};
+        acc = df_add(acc, o);
+    }
+    if (lane == 0) red[wid] = (double)acc.hi + (double)acc.lo;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
