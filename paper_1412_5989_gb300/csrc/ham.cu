@@ -181,10 +181,10 @@ __device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F,
                                            int e, int64_t colj, int idx, int sgn)
 {
     if (MODE == 1) {
-        R.col[e] = (int32_t)colj;
+        __stcs(R.col + e, (int32_t)colj);                         // evict-first: the walk's tables stay in L2
         if (K1) {                                                // K = 1: stride 1 in either layout
             const float v = __ldg(F.tbme + idx);
-            R.val[e] = sgn ? -v : v;
+            __stcs(R.val + e, sgn ? -v : v);
         } else {
             // K sets: the value of set k goes to val[e * es + k * ks]; the sign flips bit 31
             const float *t = F.tbme + (int64_t)idx * F.tb_si;
@@ -602,7 +602,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     const unsigned smk = __ballot_sync(0xffffffffu, slow);
                     const int e = pos + __popc(bm & lt);
                     if (MODE == 1 && coop) {
-                        if (in && !slow) R.col[e] = (int32_t)(cbp + y);
+                        if (in && !slow) __stcs(R.col + e, (int32_t)(cbp + y));
                         put_values_coop(F, R, in && !slow, tb >> 1, tb & 1, e);
                     } else if (in && !slow) {
                         put_single<MODE, K1>(B, F, Gr, R, e, cbp + y, tb >> 1, tb & 1);
@@ -658,8 +658,8 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 const int ins1 = self1 && !two1 ? self_rel - s1 : -1;
                 // n itself: written (pp two-move) or deferred (one-proton move) by its candidate's lane
                 if (MODE == 1 && coop) {
-                    if (self0 && two0) R.col[ex0] = r0.x + n;
-                    if (self1 && two1) R.col[ex1] = r1.x + n;
+                    if (self0 && two0) __stcs(R.col + ex0, r0.x + n);
+                    if (self1 && two1) __stcs(R.col + ex1, r1.x + n);
                     put_values_coop(F, R, self0 && two0, (int)((uint32_t)r0.z >> 1), r0.z & 1, ex0);
                     put_values_coop(F, R, self1 && two1, (int)((uint32_t)r1.z >> 1), r1.z & 1, ex1);
                 } else {
@@ -726,7 +726,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                             at = sg4.w + e + (e >= sx.y ? 1 : 0);
                             const int2 ent = n1row[sx.x + e];
                             idx = pn_index<WARPS>(sb, (uint32_t)sg4.y, (uint32_t)sg4.z, (uint32_t)ent.y, sg);
-                            if (MODE == 1 && coop) R.col[at] = sg4.x + ent.x;
+                            if (MODE == 1 && coop) __stcs(R.col + at, sg4.x + ent.x);
                             else put_single<MODE, K1>(B, F, Gr, R, at, (int64_t)(sg4.x + ent.x), idx, sg);
                         }
                         if (MODE == 1 && coop) put_values_coop(F, R, e < Tpn, idx, sg, at);
