@@ -117,6 +117,9 @@ struct SpeciesBuild {
     int32_t n_sd, n_orb, moff, mspan, Nsub_max;
     const int32_t *hash;        // open-addressing table of sub-det indices, -1 = empty
     uint32_t hash_mask;         // capacity - 1 (power of two)
+    const uint64_t *bitsT;      // W x n_sd: the bit strings word-major (coalesced scans)
+    const int32_t *orb_upto;    // [N]: orbitals with shell <= N (orbitals are ordered by shell)
+    int32_t maxN;               // highest orbital shell
 };
 
 // ---------------------------------------------------------------- host side

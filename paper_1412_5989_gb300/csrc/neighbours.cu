@@ -491,12 +491,27 @@ __global__ void k_forward_staged(SpeciesBuild S, const int32_t *cls_of, const in
         for (int y0 = (int)x + 1; y0 < end; y0 += 32) {
             const int y = y0 + lane;
             bool hit = false;
-            if (y < end) hit = xor_pop<W>(bx, S.bits + (int64_t)y * W) <= 4;
+            if (y < end) {                               // word-major copy: the warp's reads coalesce
+                int d = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) d += __popcll(bx[w] ^ S.bitsT[(int64_t)w * S.n_sd + y]);
+                hit = d <= 4;
+            }
             const unsigned msk = __ballot_sync(0xffffffffu, hit);
             if (hit) out[pos + __popc(msk & ((1u << lane) - 1))] = y;
             pos += __popc(msk);
         }
         if (lane == 0) cnt[x] = pos;
+    }
+}
+
+// bitsT[w * n + x] = bits[x * W + w]
+__global__ void k_bits_T(int64_t n, int W, const uint64_t *bits, uint64_t *bitsT)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * W; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = t / W;
+        const int w = (int)(t - x * W);
+        bitsT[(int64_t)w * n + x] = bits[t];
     }
 }
 
@@ -535,10 +550,13 @@ __global__ void k_onemove_staged(SpeciesBuild S, int cap, int64_t *cnt, int32_t 
                 const int r = w * 64 + __ffsll((long long)occ) - 1;
                 occ &= occ - 1;
                 const int Nr = S.oN[r];
-                for (int a0 = 0; a0 < S.n_orb; a0 += 32) {
+                // targets a with Nx - Nr + N_a <= Nsub_max: a prefix of the shell-ordered orbitals
+                const int lim = S.Nsub_max - Nx + Nr;
+                const int aend = lim < 0 ? 0 : lim >= S.maxN ? S.n_orb : S.orb_upto[lim];
+                for (int a0 = 0; a0 < aend; a0 += 32) {
                     const int a = a0 + lane;
                     int found = -1;
-                    if (a < S.n_orb && !((bx[a >> 6] >> (a & 63)) & 1) && Nx - Nr + S.oN[a] <= S.Nsub_max) {
+                    if (a < aend && !((bx[a >> 6] >> (a & 63)) & 1) && Nx - Nr + S.oN[a] <= S.Nsub_max) {
                         uint64_t yb[W];
 #pragma unroll
                         for (int v = 0; v < W; ++v) yb[v] = bx[v];
@@ -871,6 +889,24 @@ int species_upload(cih_basis &b, int t, const SpeciesHost &H, cudaStream_t st)
         return cuda_fail(cudaGetLastError(), "hash table");
     S.hash = table;
     S.hash_mask = cap - 1;
+    uint64_t *bitsT;
+    if ((rc = dev_alloc(b, &bitsT, std::max<size_t>((size_t)s.n_sd * W, 1)))) return rc;
+    if (s.n_sd > 0) {
+        count_launches(1);
+        k_bits_T<<<grid_for(((int64_t)s.n_sd * W + 31) / 32), 256, 0, st>>>(s.n_sd, W, d_bits, bitsT);
+    }
+    S.bitsT = bitsT;
+    int maxN = 0;
+    for (int a = 0; a < s.n_orb; ++a) maxN = std::max(maxN, s.oN[a]);
+    std::vector<int32_t> upto(maxN + 1, 0);
+    for (int a = 0; a < s.n_orb; ++a) upto[s.oN[a]] += 1;
+    for (int k = 1; k <= maxN; ++k) upto[k] += upto[k - 1];
+    for (int a = 1; a < s.n_orb; ++a)
+        if (s.oN[a] < s.oN[a - 1]) return fail(CIH_ERR_UNSUPPORTED, "orbitals not ordered by shell");
+    int32_t *d_upto;
+    if ((rc = upload(b, &d_upto, upto, st))) return rc;
+    S.orb_upto = d_upto;
+    S.maxN = maxN;
     const int hg = (int)std::min<int64_t>((s.n_sd + 255) / 256 + 1, 65535);
     count_launches(1);
     if (W == 1) k_hash_build<1><<<hg, 256, 0, st>>>(S, table);
