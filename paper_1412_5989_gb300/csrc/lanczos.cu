@@ -180,14 +180,15 @@ __global__ void k_split(int64_t n, const double *x, const double *sc, float2 *xs
 
 // K >= 32: lanes over sets, two per lane per pass; K < 32 (KS = next power
 // of two): 32/KS lane groups split the row's nonzeros, four at a time per
-// group, and the groups' row sums are reduced at the end.  The matrix is
-// read with evict-first loads, so that its stream does not push x and the
-// accumulators out of L2.  Each block walks
+// group, and the groups' row sums are reduced at the end.  With K < 32 the
+// matrix is read with evict-first loads, so that its stream does not push x
+// and the accumulators out of L2 (with lanes over sets the same hint ran
+// slower).  Each block walks
 // one contiguous run of rows, so that rows of one proton sub-determinant
 // (which touch the same x and accumulator blocks) share its L1.
 template <int KS>
 __global__ void __launch_bounds__(kThreads, 4) k_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t *col, const float *vem,
-                       const float2 *xs, const float2 *xm, float2 *yrow, unsigned long long *yfix, int s_lo, int s_hi)
+                       const float2 *xs, const float2 *xm, float2 *yrow, unsigned long long *yfix)
 {
     const int lane = threadIdx.x & 31;
     const int64_t per = (dim + gridDim.x - 1) / gridDim.x;
@@ -196,9 +197,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_spmv(int64_t dim, int K, const 
     for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += wpb) {
         const int64_t a0 = rowptr[i], a1 = rowptr[i + 1];
         if (KS >= 32) {
-            for (int s0 = s_lo; s0 < s_hi; s0 += 64) {
+            for (int s0 = 0; s0 < K; s0 += 64) {
                 const int sa = s0 + lane, sb = s0 + 32 + lane;
-                const bool ha = sa < s_hi, hb = sb < s_hi;
+                const bool ha = sa < K, hb = sb < K;
                 const float2 Xa = ha ? xm[i * K + sa] : make_float2(0.f, 0.f);
                 const float2 Xb = hb ? xm[i * K + sb] : make_float2(0.f, 0.f);
                 DF acc_a = df_of(0.f), acc_b = df_of(0.f);
@@ -208,9 +209,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_spmv(int64_t dim, int K, const 
                     float va[4], vb[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        c[u] = __ldcs(col + k + u);
-                        va[u] = ha ? __ldcs(vem + (k + u) * K + sa) : 0.f;
-                        vb[u] = hb ? __ldcs(vem + (k + u) * K + sb) : 0.f;
+                        c[u] = col[k + u];
+                        va[u] = ha ? vem[(k + u) * K + sa] : 0.f;
+                        vb[u] = hb ? vem[(k + u) * K + sb] : 0.f;
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -223,8 +224,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_spmv(int64_t dim, int K, const 
                     }
                 }
                 for (; k < a1; ++k) {
-                    const int64_t c = __ldcs(col + k);
-                    const float va = ha ? __ldcs(vem + k * K + sa) : 0.f, vb = hb ? __ldcs(vem + k * K + sb) : 0.f;
+                    const int64_t c = col[k];
+                    const float va = ha ? vem[k * K + sa] : 0.f, vb = hb ? vem[k * K + sb] : 0.f;
                     if (ha) acc_a = df_add(acc_a, df_prod(va, xs[c * K + sa]));
                     if (hb) acc_b = df_add(acc_b, df_prod(vb, xs[c * K + sb]));
                     if (c != i) {
@@ -288,18 +289,17 @@ __global__ void k_sym_finish(int64_t n, const double *sc, const float2 *yrow, do
 }
 
 // One product's k_spmv launch.  (Passes of 32 sets, to keep a share of the
-// randomly accessed vectors L2-resident at 64 sets, ran slower: 11.6 against
-// 7.7 ms per Lanczos step at 4+4 Nmax=4.)
+// randomly accessed vectors L2-resident at 64 sets, ran slower.)
 void launch_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t *col, const float *vem, const float2 *xs,
                  const float2 *xm, float2 *yrow, unsigned long long *yfix, int gr, cudaStream_t st)
 {
     count_launches(1);
-    if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix, 0, K);
-    else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix, 0, K);
-    else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix, 0, K);
-    else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix, 0, K);
-    else if (K <= 8) k_spmv<8><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix, 0, K);
-    else k_spmv<16><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix, 0, K);
+    if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else if (K <= 8) k_spmv<8><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else k_spmv<16><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
 }
 
 // partial[(r * K + s) * gridDim.x + blk] = sum over this block's rows of V[r][i][s] w[i][s]
