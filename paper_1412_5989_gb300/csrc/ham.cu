@@ -353,6 +353,43 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
             }
             __syncwarp();
             const int ne = min(per, ns - e0);
+            const int L4 = F.K >> 2;
+            if (F.em && F.vec4 && L4 <= 32 && 32 % L4 == 0) {
+                // element-major values: K/4 lanes per element with float4 reads and
+                // writes, 32 / (K/4) elements at a time; each set's sum in the same
+                // order as below
+                const int P = 32 / L4, sub = lane / L4, q4 = lane % L4;
+                for (int j0 = 0; j0 < ne; j0 += P) {
+                    const int j = j0 + sub;
+                    if (j >= ne) continue;
+                    const int e = e0 + j;
+                    const uint32_t code = w_scode[e];
+                    const int base = (code >> 31) ? nbase : 0;
+                    const int a = base + (int)(code & 0xFF), c = base + (int)((code >> 8) & 0xFF);
+                    const int sgn = (code >> 16) & 1;
+                    const int eo = w_spos[e];
+                    const DF t1v = onebody_term(B, F, a, c, status);
+                    const int2 *sj = spec + j * sp_n;
+                    DF v0 = t1v, v1 = t1v, v2 = t1v, v3 = t1v;
+#pragma unroll 8
+                    for (int i = 0; i < sp_n; ++i) {
+                        const int2 q = sj[i];
+                        if (q.x < 0) continue;
+                        float4 t = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)q.x * F.K) + q4);
+                        if (q.y < 0) { t.x = -t.x; t.y = -t.y; t.z = -t.z; t.w = -t.w; }
+                        v0 = df_add(v0, df_of(t.x));
+                        v1 = df_add(v1, df_of(t.y));
+                        v2 = df_add(v2, df_of(t.z));
+                        v3 = df_add(v3, df_of(t.w));
+                    }
+                    float4 r = make_float4(df_round(v0), df_round(v1), df_round(v2), df_round(v3));
+                    if (sgn) { r.x = -r.x; r.y = -r.y; r.z = -r.z; r.w = -r.w; }
+                    __stcs(reinterpret_cast<float4 *>(R.val + (int64_t)eo * R.es) + q4, r);
+                    if (q4 == 0) R.col[eo] = w_scol[e];
+                }
+                __syncwarp();
+                continue;
+            }
             for (int j = 0; j < ne; ++j) {
                 const int e = e0 + j;
                 const uint32_t code = w_scode[e];
@@ -536,7 +573,30 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     const float2 q = e1[w_occ[i]];
                     one = df_add(one, DF{q.x, q.y});
                 }
-                for (int k = lane; k < F.K; k += 32) {
+                const int L4 = F.K >> 2;
+                if (F.em && F.vec4 && L4 <= 32) {
+                    // element-major values: four sets per lane, float4 reads, the same
+                    // per-set order as below
+                    for (int q4 = lane; q4 < L4; q4 += 32) {
+                        DF a0 = df_of(0.f), a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll 4
+                        for (int l = 0; l < npairs; ++l) {
+                            const int32_t idx = w_scol[l];
+                            if (idx < 0) continue;
+                            float4 t = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)idx * F.K) + q4);
+                            if (w_scode[l]) { t.x = -t.x; t.y = -t.y; t.z = -t.z; t.w = -t.w; }
+                            a0 = df_add(a0, df_of(t.x));
+                            a1 = df_add(a1, df_of(t.y));
+                            a2 = df_add(a2, df_of(t.z));
+                            a3 = df_add(a3, df_of(t.w));
+                        }
+                        if (rowlen > 0)
+                            __stcs(reinterpret_cast<float4 *>(R.val) + q4,
+                                   make_float4(df_round(df_add(a0, one)), df_round(df_add(a1, one)),
+                                               df_round(df_add(a2, one)), df_round(df_add(a3, one))));
+                    }
+                }
+                for (int k = lane; k < (F.em && F.vec4 && L4 <= 32 ? 0 : F.K); k += 32) {
                     DF acc = df_of(0.f);
 #pragma unroll 4
                     for (int l = 0; l < npairs; ++l) {
