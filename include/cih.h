@@ -322,6 +322,40 @@ int cih_lanczos_lowest_em(cih_basis_h h, const int64_t *rowptr_dev, const int32_
 int cih_ham_spmv(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_dev, const float *val_dev,
                  int32_t K, int32_t values_em, const double *x_dev, double *y_dev, void *stream);
 
+/* Lanczos over row shards held by several processes (the paper distributes
+ * the matrix over processes in chunks of equal nonzero count, Sec. 2 and 4.1;
+ * cih_shard_rows and cih_ham_fill_rows build the shards).  Every process
+ * calls this with its own rows [r0, r1) (col_dev / val_dev as cih_ham_fill_rows
+ * wrote them, starting at stored nonzero rowptr[r0]) and the same other
+ * arguments; the Lanczos vectors are replicated, so all processes compute the
+ * same steps.  Each product runs on the local rows only: their row part goes
+ * to yx_dev in FP64 and the mirrored part to acc_dev in the fixed-point units
+ * of cih_ham_spmv (the scale set by f2, the squared Frobenius norm of the
+ * whole matrix's strictly-upper values: the sum of cih_ham_upper_sumsq over
+ * the shards).  The library then synchronises `stream` and calls
+ * combine(ctx), which must replace both buffers by their sums over all
+ * processes (an all-reduce: integer sums, and FP64 sums in which each entry
+ * has one nonzero term, so both exact) and return 0.  The result is the same
+ * on every process and, given the same scale, bit-identical to
+ * cih_lanczos_lowest on the whole matrix.
+ *   acc_dev: dim x K int64, yx_dev: dim x K double, both caller-owned and
+ *   zero on entry (zero again on return); other arguments as
+ *   cih_lanczos_lowest, values_em as cih_ham_spmv.
+ * Errors: as cih_lanczos_lowest; a nonzero return of combine gives
+ * CIH_ERR_ARG. */
+int cih_lanczos_lowest_shard(cih_basis_h h, const int64_t *rowptr_dev, int64_t r0, int64_t r1, const int32_t *col_dev,
+                             const float *val_dev, int32_t K, int32_t values_em, int32_t nev, int32_t max_iter,
+                             double tol, double f2, uint64_t *acc_dev, double *yx_dev, int (*combine)(void *),
+                             void *ctx, double *evals_host, double *evec0_dev, void *stream);
+
+/* One shard's part of the bound cih_lanczos_lowest_shard needs: the sum of
+ * the squares of the strictly-upper values (all K sets) of rows [r0, r1),
+ * val_dev starting at stored nonzero rowptr[r0] (set-major K x nnz_shard, or
+ * element-major when values_em == 1), into *f2_host.  Synchronises `stream`.
+ * Errors: CIH_ERR_ARG, CIH_ERR_NOMEM, CIH_ERR_CUDA. */
+int cih_ham_upper_sumsq(cih_basis_h h, const int64_t *rowptr_dev, int64_t r0, int64_t r1, const float *val_dev,
+                        int32_t K, int32_t values_em, double *f2_host, void *stream);
+
 /* Adjoint: d E0 / d t for every two-body table entry t of each of K sets,
  * given the normalised lowest eigenvectors psi (Hellmann-Feynman, E0 =
  * psi^T H psi): g_t = sum over stored (i, j) whose value uses t with sign s of

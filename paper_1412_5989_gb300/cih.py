@@ -63,6 +63,9 @@ _SIGS = {
     "cih_lanczos_lowest": [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _P, _P],
     "cih_lanczos_lowest_em": [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _P, _P],
     "cih_ham_spmv": [_P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P, _P],
+    "cih_ham_upper_sumsq": [_P, _P, C.c_int64, C.c_int64, _P, C.c_int32, C.c_int32, _dp, _P],
+    "cih_lanczos_lowest_shard": [_P, _P, C.c_int64, C.c_int64, _P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                 C.c_double, C.c_double, _P, _P, C.CFUNCTYPE(C.c_int, C.c_void_p), _P, _dp, _P, _P],
     "cih_ham_tbme_grad": [_P, _P, C.c_int32, _P, _P, _P],
     "cih_tridiag_eigen": [C.c_int32, _dp, _dp, _dp, _dp],
     "cih_kernel_launches": [_i64p],
@@ -450,6 +453,50 @@ class Basis:
                              _ptr(xx), _ptr(y), _stream(stream)), "ham_spmv")
         return y
 
+    def upper_sumsq(self, rowptr, r0: int, r1: int, val, element_major: bool = False, stream=None) -> float:
+        """Sum of the squares of the strictly-upper values of rows r0 .. r1 - 1
+        (all sets), val as fill_rows returns it (cih_ham_upper_sumsq)."""
+        v = (val if val.dim() == 2 else val.unsqueeze(0)).contiguous()
+        K = v.shape[1] if element_major else v.shape[0]
+        out = C.c_double()
+        _ok(lib.cih_ham_upper_sumsq(self._h, _ptr(rowptr), r0, r1, _ptr(v), K, 1 if element_major else 0,
+                                    C.byref(out), _stream(stream)), "ham_upper_sumsq")
+        return out.value
+
+    def lanczos_shard(self, rowptr, r0: int, r1: int, col, val, f2: float, combine, nev: int = 5,
+                      max_iter: int = 300, tol: float = 1e-8, want_vectors: bool = True, element_major: bool = False,
+                      stream=None):
+        """This process's part of a Lanczos run over row shards
+        (cih_lanczos_lowest_shard).  f2: the whole matrix's sum of
+        upper_sumsq over the shards; combine(acc, yx) must replace the two
+        buffers (dim * K int64 and float64 CUDA tensors) by their sums over all
+        processes.  Returns (evals (K, nev), evec0 (K, dim) or None, converged)."""
+        import torch
+        v = (val if val.dim() == 2 else val.unsqueeze(0)).contiguous()
+        K = v.shape[1] if element_major else v.shape[0]
+        acc = torch.zeros(self.dim * K, dtype=torch.int64, device="cuda")
+        yx = torch.zeros(self.dim * K, dtype=torch.float64, device="cuda")
+        err = []
+
+        def cb(_ctx):
+            try:
+                combine(acc, yx)
+                return 0
+            except Exception as e:                                # reported after the call returns
+                err.append(e)
+                return 1
+
+        cfun = lib.cih_lanczos_lowest_shard.argtypes[14](cb)
+        ev = np.zeros((K, nev))
+        vec = torch.empty((K, self.dim), dtype=torch.float64, device="cuda") if want_vectors else None
+        rc = lib.cih_lanczos_lowest_shard(self._h, _ptr(rowptr), r0, r1, _ptr(col), _ptr(v), K,
+                                          1 if element_major else 0, nev, max_iter, tol, float(f2), _ptr(acc),
+                                          _ptr(yx), cfun, None, ev.ctypes.data_as(_dp), _ptr(vec), _stream(stream))
+        if err:
+            raise err[0]
+        rc = _ok(rc, "lanczos_lowest_shard")
+        return ev, vec, rc == 0
+
     def tbme_grad(self, rowptr, psi, stream=None):
         """d E0 / d table entry for each set: (K, tbme_len) float64 CUDA tensor."""
         import torch
@@ -540,6 +587,33 @@ class _Lazy:
 
 
 _LowestEigenvalue = _Lazy()
+
+
+def lanczos_distributed(basis: Basis, rowptr, r0: int, r1: int, col, val, nev: int = 5, max_iter: int = 300,
+                        tol: float = 1e-8, group=None, want_vectors: bool = True, element_major: bool = False):
+    """Lanczos over the row shards of a torch.distributed group: this process
+    holds rows r0 .. r1 - 1 (fill_rows); the bound and the two buffers of
+    every product are summed with all_reduce (on the device with NCCL, else
+    through host copies).  Every process gets the same result."""
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    f2 = torch.tensor([basis.upper_sumsq(rowptr, r0, r1, val, element_major)], dtype=torch.float64, device=dev)
+    dist.all_reduce(f2, group=group)
+
+    def combine(acc, yx):
+        if dev == "cuda":
+            dist.all_reduce(acc, group=group)
+            dist.all_reduce(yx, group=group)
+            return
+        a, y = acc.cpu(), yx.cpu()
+        dist.all_reduce(a, group=group)
+        dist.all_reduce(y, group=group)
+        acc.copy_(a)
+        yx.copy_(y)
+
+    return basis.lanczos_shard(rowptr, r0, r1, col, val, float(f2.item()), combine, nev, max_iter, tol,
+                               want_vectors, element_major)
 
 
 def build_hamiltonian(basis: Basis, tbme, hbar_omega: float = 20.0, e_sp=None, stream=None):

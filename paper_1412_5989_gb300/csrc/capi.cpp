@@ -477,6 +477,49 @@ int cih_ham_spmv(cih_basis_h h, const int64_t *rowptr_dev, const int32_t *col_de
     });
 }
 
+int cih_ham_upper_sumsq(cih_basis_h h, const int64_t *rowptr_dev, int64_t r0, int64_t r1, const float *val_dev,
+                        int32_t K, int32_t values_em, double *f2_host, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!f2_host) return fail(CIH_ERR_ARG, "NULL output");
+    *f2_host = 0.0;
+    if (K < 1 || K > 256 || (values_em != 0 && values_em != 1)) return fail(CIH_ERR_ARG, "K or values_em out of range");
+    if (r0 < 0 || r1 < r0 || r1 > h->dim) return fail(CIH_ERR_ARG, "row range outside 0 .. dim");
+    if (r1 == r0) return CIH_OK;
+    if (!rowptr_dev || !val_dev) return fail(CIH_ERR_ARG, "NULL array");
+    return guarded([&]() -> int {
+        return upper_sumsq(*h, rowptr_dev, r0, r1, val_dev, K, values_em != 0, f2_host, (cudaStream_t)stream);
+    });
+}
+
+int cih_lanczos_lowest_shard(cih_basis_h h, const int64_t *rowptr_dev, int64_t r0, int64_t r1, const int32_t *col_dev,
+                             const float *val_dev, int32_t K, int32_t values_em, int32_t nev, int32_t max_iter,
+                             double tol, double f2, uint64_t *acc_dev, double *yx_dev, int (*combine)(void *),
+                             void *ctx, double *evals_host, double *evec0_dev, void *stream)
+{
+    int rc = needs_device(h);
+    if (rc) return rc;
+    if (!rowptr_dev || !evals_host || !acc_dev || !yx_dev || !combine) return fail(CIH_ERR_ARG, "NULL array or callback");
+    if (K < 1 || K > 256 || nev < 1 || nev > 64 || max_iter < 1 || max_iter > 2048 || !(tol > 0) ||
+        (values_em != 0 && values_em != 1) || !(f2 >= 0))
+        return fail(CIH_ERR_ARG, "K, nev, max_iter, tol, values_em or f2 out of range");
+    if (r0 < 0 || r1 < r0 || r1 > h->dim) return fail(CIH_ERR_ARG, "row range outside 0 .. dim");
+    if (r1 > r0 && (!col_dev || !val_dev)) return fail(CIH_ERR_ARG, "NULL array");
+    ShardRun sh;
+    sh.r0 = r0;
+    sh.r1 = r1;
+    sh.f2 = f2;
+    sh.acc = reinterpret_cast<unsigned long long *>(acc_dev);
+    sh.yx = yx_dev;
+    sh.combine = combine;
+    sh.ctx = ctx;
+    return guarded([&]() -> int {
+        return lanczos(*h, rowptr_dev, col_dev, val_dev, K, nev, max_iter, tol, evals_host, evec0_dev,
+                       (cudaStream_t)stream, values_em != 0, &sh);
+    });
+}
+
 int cih_ham_tbme_grad(cih_basis_h h, const int64_t *rowptr_dev, int32_t K, const double *psi_dev,
                       double *grad_dev, void *stream)
 {

@@ -284,9 +284,25 @@ void tridiag_qr_last(int n, std::vector<double> &d, std::vector<double> e, std::
 void tridiag_eigenvector(int n, const double *d, const double *e, double theta, double *z);
 
 // Lanczos (lanczos.cu)
+// A row shard's part of a Lanczos run over several processes: its rows, the
+// whole matrix's squared strictly-upper Frobenius norm (summed over the
+// shards), and two caller buffers (dim x K, zero on entry) that `combine`
+// sums over the shards in place after each product.
+struct ShardRun {
+    int64_t r0 = 0, r1 = 0;
+    double f2 = 0.0;
+    unsigned long long *acc = nullptr;
+    double *yx = nullptr;
+    int (*combine)(void *ctx) = nullptr;
+    void *ctx = nullptr;
+};
 int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val,
             int K, int nev, int max_iter, double tol, double *evals, double *evec0, cudaStream_t st,
-            bool values_em = false);
+            bool values_em = false, const ShardRun *sh = nullptr);
+// the sum of squares of the strictly-upper values of rows [r0, r1) (all K
+// sets), the arrays starting at rowptr[r0]: one shard's part of the bound
+int upper_sumsq(const cih_basis &b, const int64_t *rowptr, int64_t r0, int64_t r1, const float *val, int K,
+                bool values_em, double *f2, cudaStream_t st);
 // device bytes lanczos() allocates for a call
 int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter);
 // y = H x for K sets from the stored upper half (x, y element-major: x[i * K + s])

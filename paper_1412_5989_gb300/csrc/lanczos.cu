@@ -55,6 +55,12 @@ __global__ void k_vals_em(int K, int64_t nnz, const float *val, float *vem)
     }
 }
 
+// Rows [r0, r1) of the matrix whose column and value arrays start at stored
+// nonzero `base` (0 for a whole matrix; rowptr[r0] for a row shard).
+struct RowRange {
+    int64_t r0, r1, base;
+};
+
 // ---- y = H x from the stored upper half, each stored nonzero read once.
 //
 // Row i's warp forms the row part sum_j h_ij x_j in FP64 registers (a fixed
@@ -74,16 +80,17 @@ __global__ void k_vals_em(int K, int64_t nnz, const float *val, float *vem)
 // values of all sets (a warp per row, lanes over (nonzero, set) pairs), in
 // double-float sums of the exact FP32-pair squares
 constexpr int kSumsqThreads = 1024;
-__global__ void __launch_bounds__(kSumsqThreads) k_upper_sumsq(int64_t dim, int K, const int64_t *rowptr,
+__global__ void __launch_bounds__(kSumsqThreads) k_upper_sumsq(RowRange rr, int K, const int64_t *rowptr,
                                                                const float *vem, double *partial)
 {
     __shared__ double red[kSumsqThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     DF acc = df_of(0.f);
-    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid; i < dim; i += (int64_t)gridDim.x * (blockDim.x >> 5)) {
-        const int64_t t1 = rowptr[i + 1] * K;
+    for (int64_t i = rr.r0 + blockIdx.x * (int64_t)(blockDim.x >> 5) + wid; i < rr.r1;
+         i += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+        const int64_t t1 = (rowptr[i + 1] - rr.base) * K;
 #pragma unroll 4
-        for (int64_t t = (rowptr[i] + 1) * K + lane; t < t1; t += 32) {
+        for (int64_t t = (rowptr[i] - rr.base + 1) * K + lane; t < t1; t += 32) {
             const float v = vem[t];
             const float p = v * v;
             acc = df_add(acc, DF{p, fmaf(v, v, -p)});
@@ -187,15 +194,15 @@ __global__ void k_split(int64_t n, const double *x, const double *sc, float2 *xs
 // one contiguous run of rows, so that rows of one proton sub-determinant
 // (which touch the same x and accumulator blocks) share its L1.
 template <int KS>
-__global__ void __launch_bounds__(kThreads, 4) k_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t *col, const float *vem,
+__global__ void __launch_bounds__(kThreads, 4) k_spmv(RowRange rr, int K, const int64_t *rowptr, const int32_t *col, const float *vem,
                        const float2 *xs, const float2 *xm, float2 *yrow, unsigned long long *yfix)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t per = (dim + gridDim.x - 1) / gridDim.x;
-    const int64_t r0 = blockIdx.x * per, r1 = min(dim, r0 + per);
+    const int64_t per = (rr.r1 - rr.r0 + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = rr.r0 + blockIdx.x * per, r1 = min(rr.r1, r0 + per);
     const int wpb = blockDim.x >> 5;
     for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += wpb) {
-        const int64_t a0 = rowptr[i], a1 = rowptr[i + 1];
+        const int64_t a0 = rowptr[i] - rr.base, a1 = rowptr[i + 1] - rr.base;
         if (KS >= 32) {
             for (int s0 = 0; s0 < K; s0 += 64) {
                 const int sa = s0 + lane, sb = s0 + 32 + lane;
@@ -288,18 +295,42 @@ __global__ void k_sym_finish(int64_t n, const double *sc, const float2 *yrow, do
     }
 }
 
+// Row shards: the local rows' row part in FP64 into yx (the other entries
+// stay 0, so that a sum over the shards is exact); then, once the caller has
+// summed yx and the accumulators over the shards, y = yx + acc 2^-s and both
+// are cleared.  The same operations in the same order as k_sym_finish.
+__global__ void k_shard_rows(RowRange rr, int K, const double *sc, const float2 *yrow, double *yx)
+{
+    const double rinv = sc[3];
+    const int64_t n = (rr.r1 - rr.r0) * K, o = rr.r0 * K;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const float2 r = yrow[o + t];
+        yx[o + t] = ((double)r.x + (double)r.y) * rinv;
+    }
+}
+
+__global__ void k_shard_finish(int64_t n, const double *sc, double *yx, unsigned long long *acc, double *y)
+{
+    const double sinv = sc[1];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        y[t] = yx[t] + (double)(long long)acc[t] * sinv;
+        yx[t] = 0.0;
+        acc[t] = 0ull;
+    }
+}
+
 // One product's k_spmv launch.  (Passes of 32 sets, to keep a share of the
 // randomly accessed vectors L2-resident at 64 sets, ran slower.)
-void launch_spmv(int64_t dim, int K, const int64_t *rowptr, const int32_t *col, const float *vem, const float2 *xs,
+void launch_spmv(RowRange rr, int K, const int64_t *rowptr, const int32_t *col, const float *vem, const float2 *xs,
                  const float2 *xm, float2 *yrow, unsigned long long *yfix, int gr, cudaStream_t st)
 {
     count_launches(1);
-    if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
-    else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
-    else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
-    else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
-    else if (K <= 8) k_spmv<8><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
-    else k_spmv<16><<<gr, kThreads, 0, st>>>(dim, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else if (K <= 8) k_spmv<8><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else k_spmv<16><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
 }
 
 // partial[(r * K + s) * gridDim.x + blk] = sum over this block's rows of V[r][i][s] w[i][s]
@@ -413,18 +444,35 @@ int64_t lanczos_bytes(int64_t dim, int64_t nnz, int K, int max_iter)
     return bytes + 8 * 256;                                         // allocation granules
 }
 
+// sh->f2 -> (2^s, 2^-s, 1, 1): the scale k_mirror_scale gives unit vectors
+static void shard_scale(double f2, double *sc)
+{
+    int e = 0;
+    if (f2 > 0.0) (void)std::frexp(std::sqrt(f2) * (1.0 + 1e-6), &e);
+    const int sh = std::min(60 - e, 124 - 1);
+    sc[0] = std::ldexp(1.0, sh);
+    sc[1] = std::ldexp(1.0, -sh);
+    sc[2] = sc[3] = 1.0;
+}
+
 int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const float *val, int K, int nev,
-            int max_iter, double tol, double *evals, double *evec0, cudaStream_t st, bool values_em)
+            int max_iter, double tol, double *evals, double *evec0, cudaStream_t st, bool values_em,
+            const ShardRun *sh)
 {
     const int64_t dim = b.dim;
     for (int k = 0; k < K * nev; ++k) evals[k] = NAN;
     if (dim == 0) return CIH_OK;
     if (K > kThreads) return fail(CIH_ERR_UNSUPPORTED, "lanczos: at most 256 sets per call");
     if (dim > INT32_MAX) return fail(CIH_ERR_UNSUPPORTED, "lanczos: dimension above 2^31");
-    int64_t nnz = 0;
-    cudaError_t e = cudaMemcpyAsync(&nnz, rowptr + dim, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    // the rows this process multiplies, and the stored nonzeros its arrays hold
+    const int64_t r0 = sh ? sh->r0 : 0, r1 = sh ? sh->r1 : dim;
+    int64_t ends[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(&ends[0], rowptr + r0, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], rowptr + r1, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "lanczos: read nnz");
+    const int64_t base = sh ? ends[0] : 0, nnz = ends[1] - base;
+    const RowRange rr{r0, r1, base};
     const int m_max = (int)std::min<int64_t>(max_iter, dim);
     const int64_t vstride = dim * K;
 
@@ -441,7 +489,7 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
     unsigned long long *yfix = nullptr;
     float2 *xs = nullptr, *xm = nullptr, *yrow = nullptr;
     double *V = nullptr, *w = nullptr, *partial = nullptr, *hdev = nullptr, *fdev = nullptr, *sc = nullptr;
-    bool ok = alloc((void **)&yfix, sizeof(unsigned long long) * (size_t)vstride) &&
+    bool ok = (sh ? (yfix = sh->acc) != nullptr : alloc((void **)&yfix, sizeof(unsigned long long) * (size_t)vstride)) &&
               alloc((void **)&xs, sizeof(float2) * (size_t)vstride) &&
               alloc((void **)&xm, sizeof(float2) * (size_t)vstride) &&
               alloc((void **)&yrow, sizeof(float2) * (size_t)vstride) &&
@@ -453,9 +501,10 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
     if (ok && K > 1 && !values_em) ok = alloc((void **)&vem, sizeof(float) * (size_t)nnz * K);
     int rc = ok ? CIH_OK : fail(CIH_ERR_NOMEM, "lanczos: device memory");
     const int g = grid_for(vstride);
-    const int gr = (int)std::min<int64_t>((dim + 7) / 8, 152 * 32);
+    const int gr = (int)std::max<int64_t>(1, std::min<int64_t>((r1 - r0 + 7) / 8, 152 * 32));
 
-    // element-major values, the mirror scale and cleared accumulators (no host synchronisation)
+    // element-major values, the mirror scale and cleared accumulators (no host
+    // synchronisation; a shard's scale comes from the whole matrix's norm)
     if (!rc) {
         if (K > 1 && !values_em) {
             count_launches(1);
@@ -463,17 +512,36 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
         } else {
             vem = const_cast<float *>(val);                         // K = 1, or already element-major
         }
-        cudaMemsetAsync(yfix, 0, sizeof(unsigned long long) * (size_t)vstride, st);
-        count_launches(2);
-        k_upper_sumsq<<<kDotBlocks, kSumsqThreads, 0, st>>>(dim, K, rowptr, vem, partial);
-        k_mirror_scale<<<1, 32, 0, st>>>(kDotBlocks, partial, K, nullptr, sc);
+        if (sh) {
+            double hsc[4];
+            shard_scale(sh->f2, hsc);
+            e = cudaMemcpyAsync(sc, hsc, sizeof(hsc), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "lanczos: shard scale");
+        } else {
+            cudaMemsetAsync(yfix, 0, sizeof(unsigned long long) * (size_t)vstride, st);
+            count_launches(2);
+            k_upper_sumsq<<<kDotBlocks, kSumsqThreads, 0, st>>>(rr, K, rowptr, vem, partial);
+            k_mirror_scale<<<1, 32, 0, st>>>(kDotBlocks, partial, K, nullptr, sc);
+        }
     }
 
-    auto spmv = [&](const double *x, double *y) {
+    auto spmv = [&](const double *x, double *y) -> int {
         count_launches(2);
         k_split<<<g, kThreads, 0, st>>>(vstride, x, sc, xs, xm);
-        launch_spmv(dim, K, rowptr, col, vem, xs, xm, yrow, yfix, gr, st);
-        k_sym_finish<<<g, kThreads, 0, st>>>(vstride, sc, yrow, y, yfix);
+        launch_spmv(rr, K, rowptr, col, vem, xs, xm, yrow, yfix, gr, st);
+        if (!sh) {
+            k_sym_finish<<<g, kThreads, 0, st>>>(vstride, sc, yrow, y, yfix);
+            return CIH_OK;
+        }
+        // a shard: its rows' row part, then the caller sums both buffers over the shards
+        count_launches(2);
+        k_shard_rows<<<grid_for((r1 - r0) * K), kThreads, 0, st>>>(rr, K, sc, yrow, sh->yx);
+        cudaError_t ee = cudaStreamSynchronize(st);
+        if (ee != cudaSuccess) return cuda_fail(ee, "lanczos: shard product");
+        if (sh->combine(sh->ctx) != 0) return fail(CIH_ERR_ARG, "lanczos: the shard combine callback failed");
+        k_shard_finish<<<g, kThreads, 0, st>>>(vstride, sc, sh->yx, yfix, y);
+        return CIH_OK;
     };
     // h[r][s] = V[r] . w for r < nvec: into hdev (device) and hh (host)
     std::vector<double> hh((size_t)(m_max + 1) * K);
@@ -506,7 +574,7 @@ int lanczos(const cih_basis &b, const int64_t *rowptr, const int32_t *col, const
     std::vector<double> theta((size_t)K * nev, NAN);
     int m = 0;
     for (int j = 0; j < m_max && !rc; ++j) {
-        spmv(V + (int64_t)j * vstride, w);
+        if ((rc = spmv(V + (int64_t)j * vstride, w))) break;
         for (int pass = 0; pass < 2 && !rc; ++pass) {
             if ((rc = dots(V, j + 1, w))) break;
             for (int s = 0; s < K; ++s)                             // alpha_j = v_j . H v_j (+ the
@@ -624,18 +692,60 @@ int ham_spmv(const cih_basis &b, const int64_t *rowptr, const int32_t *col, cons
         }
         cudaMemsetAsync(yfix, 0, sizeof(unsigned long long) * (size_t)n, st);
         count_launches(6);
-        k_upper_sumsq<<<kDotBlocks, kSumsqThreads, 0, st>>>(dim, K, rowptr, vem, partial);
+        k_upper_sumsq<<<kDotBlocks, kSumsqThreads, 0, st>>>(RowRange{0, dim, 0}, K, rowptr, vem, partial);
         k_dots<<<dim3(kDotBlocks, 1), kThreads, 0, st>>>(dim, K, 1, x, n, x, xpart);
         k_dots_finish<<<(K + 255) / 256, 256, 0, st>>>(K, kDotBlocks, xpart, xn2);
         k_mirror_scale<<<1, 32, 0, st>>>(kDotBlocks, partial, K, xn2, sc);
         k_split<<<grid_for(n), kThreads, 0, st>>>(n, x, sc, xs, xm);
         const int gr = (int)std::min<int64_t>((dim + 7) / 8, 152 * 32);
-        launch_spmv(dim, K, rowptr, col, vem, xs, xm, yrow, yfix, gr, st);
+        launch_spmv(RowRange{0, dim, 0}, K, rowptr, col, vem, xs, xm, yrow, yfix, gr, st);
         k_sym_finish<<<grid_for(n), kThreads, 0, st>>>(n, sc, yrow, y, yfix);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "spmv kernels");
     }
     for (void *p : bufs) cudaFreeAsync(p, st);
+    return rc;
+}
+
+
+int upper_sumsq(const cih_basis &b, const int64_t *rowptr, int64_t r0, int64_t r1, const float *val, int K,
+                bool values_em, double *f2, cudaStream_t st)
+{
+    *f2 = 0.0;
+    if (r1 <= r0) return CIH_OK;
+    if (K > kThreads) return fail(CIH_ERR_UNSUPPORTED, "upper_sumsq: at most 256 sets per call");
+    int64_t ends[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(&ends[0], rowptr + r0, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], rowptr + r1, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "upper_sumsq: read nnz");
+    const int64_t nnz = ends[1] - ends[0];
+    float *vem = const_cast<float *>(val);
+    double *partial = nullptr;
+    if (cudaMallocFromPoolAsync((void **)&partial, sizeof(double) * kDotBlocks, b.pool, st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(CIH_ERR_NOMEM, "upper_sumsq: device memory");
+    }
+    int rc = CIH_OK;
+    if (K > 1 && !values_em) {
+        if (cudaMallocFromPoolAsync((void **)&vem, std::max<size_t>(sizeof(float) * (size_t)nnz * K, 16), b.pool, st) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaFreeAsync(partial, st);
+            return fail(CIH_ERR_NOMEM, "upper_sumsq: device memory");
+        }
+        count_launches(1);
+        k_vals_em<<<grid_for(nnz * K), kThreads, 0, st>>>(K, nnz, val, vem);
+    }
+    count_launches(1);
+    k_upper_sumsq<<<kDotBlocks, kSumsqThreads, 0, st>>>(RowRange{r0, r1, ends[0]}, K, rowptr, vem, partial);
+    std::vector<double> hp(kDotBlocks);
+    e = cudaMemcpyAsync(hp.data(), partial, sizeof(double) * kDotBlocks, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "upper_sumsq");
+    for (int k = 0; k < kDotBlocks && !rc; ++k) *f2 += hp[k];             // the order k_mirror_scale sums in
+    cudaFreeAsync(partial, st);
+    if (vem != val) cudaFreeAsync(vem, st);
     return rc;
 }
 
