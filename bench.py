@@ -119,11 +119,16 @@ def fill_traffic(fill_source_sha):
 
 
 def kernel_source_sha():
-    """Hash of the fill kernel's sources with comments and blank space removed,
-    so that only a code change invalidates a recorded capture."""
+    """Hash of what the fill kernel compiles from -- ham.cu, ham_common.cuh and
+    the device structs it reads (DevSpecies, DevBasis) -- with comments and
+    blank space removed, so that only a change of that code invalidates a
+    recorded capture."""
     h = hashlib.sha256()
-    for f in ("ham.cu", "ham_common.cuh", "cih_internal.h"):
-        src = open(os.path.join(ROOT, "paper_1412_5989_gb300", "csrc", f)).read()
+    csrc = os.path.join(ROOT, "paper_1412_5989_gb300", "csrc")
+    parts = [open(os.path.join(csrc, f)).read() for f in ("ham.cu", "ham_common.cuh")]
+    hdr = open(os.path.join(csrc, "cih_internal.h")).read()
+    parts += re.findall(r"struct (?:DevSpecies|DevBasis) \{.*?\n\};", hdr, flags=re.S)
+    for src in parts:
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
