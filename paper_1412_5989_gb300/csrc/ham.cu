@@ -313,7 +313,7 @@ __device__ __forceinline__ void put_values_coop(const FillArgs &F, const RowOut 
 // kLaneSets sets on: one element at a time, lanes over sets).
 // The queue holds row-relative positions, columns and packed moves
 // (bra-only a, ket-only c, sign, neutron flag in bit 31).
-template <int MODE, bool K1>
+template <int MODE, bool K1, bool EM>
 __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, const FillArgs &F, const GradArgs &Gr,
                                            int *status, const int16_t *w_occ, const int32_t *w_spos,
                                            const int32_t *w_scol, const uint32_t *w_scode, int &nslow,
@@ -354,7 +354,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
             __syncwarp();
             const int ne = min(per, ns - e0);
             const int L4 = F.K >> 2;
-            if (F.em && F.vec4 && L4 <= 32 && 32 % L4 == 0) {
+            if (EM) {
                 // element-major values: K/4 lanes per element with float4 reads and
                 // writes, 32 / (K/4) elements at a time; each set's sum in the same
                 // order as below
@@ -470,7 +470,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
     nslow = 0;
 }
 
-template <int W, int MODE, bool K1, int WARPS>
+template <int W, int MODE, bool K1, int WARPS, bool EM>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
 k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs Gr, int64_t r0, int64_t r1,
        int *status)
@@ -524,7 +524,10 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
     const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
     const int Zpro = B.nZ[0], Zneu = B.nZ[1];
     // K sets, element-major values: warp-cooperative value writes
-    const bool coop = MODE == 1 && !K1 && F.em && F.vec4 && ((F.K >> 2) > 32 ? (F.K >> 2) % 32 == 0 : 32 % (F.K >> 2) == 0);
+    // (EM: the launcher chose this instantiation because F.em, F.vec4 and
+    // K/4 dividing 32 or a multiple of 32 hold; the other K-set layouts
+    // compile without these paths, and these without theirs)
+    constexpr bool coop = MODE == 1 && !K1 && EM;
 
     for (int64_t row = r0 + gw; row < r1; row += nw) {
         const int p = B.row_p[row];
@@ -574,7 +577,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     one = df_add(one, DF{q.x, q.y});
                 }
                 const int L4 = F.K >> 2;
-                if (F.em && F.vec4 && L4 <= 32) {
+                if (EM && L4 <= 32) {
                     // element-major values: four sets per lane, float4 reads, the same
                     // per-set order as below
                     for (int q4 = lane; q4 < L4; q4 += 32) {
@@ -596,7 +599,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                                                df_round(df_add(a2, one)), df_round(df_add(a3, one))));
                     }
                 }
-                for (int k = lane; k < (F.em && F.vec4 && L4 <= 32 ? 0 : F.K); k += 32) {
+                for (int k = lane; k < (EM && L4 <= 32 ? 0 : F.K); k += 32) {
                     DF acc = df_of(0.f);
 #pragma unroll 4
                     for (int l = 0; l < npairs; ++l) {
@@ -656,7 +659,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 if (MODE != 0) {
                     if (MODE == 1 && pos + __popc(bm) > rowlen) { atomicOr(status, 2); break; }
                     if (nslow > kSlowCap - 32)
-                        flush_slow<MODE, K1>(B, lg, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
+                        flush_slow<MODE, K1, EM>(B, lg, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
                     const int32_t tb = in ? tbl : 0;
                     const bool slow = in && tb < 0;
                     const unsigned smk = __ballot_sync(0xffffffffu, slow);
@@ -731,7 +734,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 const bool p0 = self0 && !two0, p1 = self1 && !two1;
                 const unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
                 if (nslow + __popc(m0) + __popc(m1) > kSlowCap)
-                    flush_slow<MODE, K1>(B, lg, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
+                    flush_slow<MODE, K1, EM>(B, lg, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
                 if (p0) {
                     const int q = nslow + __popc(m0 & lt);
                     const uint32_t mv = (uint32_t)r0.w;
@@ -797,7 +800,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
             }
             pos += T;
         }
-        if (MODE != 0 && nslow > 0) flush_slow<MODE, K1>(B, lg, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
+        if (MODE != 0 && nslow > 0) flush_slow<MODE, K1, EM>(B, lg, F, Gr, status, w_occ, w_spos, w_scol, w_scode, nslow, R);
         if (MODE == 0 && lane == 0) counts[row] = pos;
         __syncwarp();
     }
@@ -899,9 +902,18 @@ int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, co
         return ee == cudaSuccess ? CIH_OK : cuda_fail(ee, "row kernel launch");
     };
     const bool k1 = MODE == 1 && F.K == 1;
-    if (b.W == 1) return k1 ? go(k_rows<1, MODE, true, WARPS>) : go(k_rows<1, MODE, false, WARPS>);
-    if (b.W == 2) return k1 ? go(k_rows<2, MODE, true, WARPS>) : go(k_rows<2, MODE, false, WARPS>);
-    return k1 ? go(k_rows<4, MODE, true, WARPS>) : go(k_rows<4, MODE, false, WARPS>);
+    const int L4 = F.K >> 2;
+    const bool em = MODE == 1 && !k1 && F.em && F.vec4 && (L4 > 32 ? L4 % 32 == 0 : 32 % L4 == 0);
+    if constexpr (MODE == 1) {
+        if (em) {                                            // element-major K sets: warp-cooperative writes
+            if (b.W == 1) return go(k_rows<1, MODE, false, WARPS, true>);
+            if (b.W == 2) return go(k_rows<2, MODE, false, WARPS, true>);
+            return go(k_rows<4, MODE, false, WARPS, true>);
+        }
+    }
+    if (b.W == 1) return k1 ? go(k_rows<1, MODE, true, WARPS, false>) : go(k_rows<1, MODE, false, WARPS, false>);
+    if (b.W == 2) return k1 ? go(k_rows<2, MODE, true, WARPS, false>) : go(k_rows<2, MODE, false, WARPS, false>);
+    return k1 ? go(k_rows<4, MODE, true, WARPS, false>) : go(k_rows<4, MODE, false, WARPS, false>);
 }
 
 template <int MODE>
