@@ -173,6 +173,7 @@ struct RowOut {
     float *val;
     int64_t es, ks;
     int64_t row;
+    long long psir;           // adjoint with one vector: the row's own psi (2^-61 units)
 };
 
 // one single-term element (table index, sign bit) at row-relative position e
@@ -237,8 +238,8 @@ __device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F,
             }
         }
     } else if (MODE == 2) {
-        for (int k = 0; k < Gr.K; ++k) {                         // w psi_i psi_j, w = 2: 2^-57 units
-            const long long q = psi_prod(Gr.psi + (int64_t)k * B.dim, R.row, colj) >> 1;
+        for (int k = 0; k < (K1 ? 1 : Gr.K); ++k) {             // w psi_i psi_j, w = 2: 2^-57 units
+            const long long q = (K1 ? __mul64hi(R.psir, Gr.psi[colj]) : psi_prod(Gr.psi + (int64_t)k * B.dim, R.row, colj)) >> 1;
             atomicAdd(Gr.acc + (int64_t)k * B.tbme_len + idx, (unsigned long long)(sgn ? -q : q));
         }
     }
@@ -445,7 +446,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
         }
         // the one-body term t_ac (one per element: added by its group's first lane)
         const DF t1v = (MODE == 1 && act && i == 0) ? onebody_term(B, F, a, c, status) : df_of(0.f);
-        for (int kk = 0; kk < (MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++kk) {
+        for (int kk = 0; kk < (K1 ? 1 : MODE == 1 ? F.K : Gr.K); ++kk) {
             if (MODE == 1) {
                 DF v = df_of(0.f);
                 if (has && ok) {
@@ -460,7 +461,8 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
                     R.val[(int64_t)eo * R.es + (int64_t)kk * R.ks] = sgn ? -r : r;
                 }
             } else if (has && ok) {
-                const long long q = psi_prod(Gr.psi + (int64_t)kk * B.dim, R.row, colj) >> 1;
+                const long long q =
+                    (K1 ? __mul64hi(R.psir, Gr.psi[colj]) : psi_prod(Gr.psi + (int64_t)kk * B.dim, R.row, colj)) >> 1;
                 const bool neg = (sgn != 0) != (sg < 0);
                 atomicAdd(Gr.acc + (int64_t)kk * B.tbme_len + idx, (unsigned long long)(neg ? -q : q));
             }
@@ -538,6 +540,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         const int64_t cbp = rbp - nbp;
         RowOut R;
         R.row = row;
+        R.psir = (MODE == 2 && K1) ? Gr.psi[row] : 0;
         R.es = (MODE == 1 && F.em) ? F.K : 1;
         R.ks = (MODE == 1 && F.em) ? 1 : nnz;
         int rowlen = 0;
@@ -613,7 +616,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 if (lane == 0 && rowlen > 0) R.col[0] = (int32_t)row;
                 __syncwarp();
             }
-            for (int k = 0; k < (kset ? 0 : MODE == 1 ? (K1 ? 1 : F.K) : Gr.K); ++k) {
+            for (int k = 0; k < (kset ? 0 : K1 ? 1 : MODE == 1 ? F.K : Gr.K); ++k) {
                 DF acc = df_of(0.f);
                 for (int l = lane; l < npairs; l += 32) {
                     const int a = w_occ[pi[l]], c = w_occ[pj[l]];
@@ -901,7 +904,7 @@ int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, co
         ee = cudaGetLastError();
         return ee == cudaSuccess ? CIH_OK : cuda_fail(ee, "row kernel launch");
     };
-    const bool k1 = MODE == 1 && F.K == 1;
+    const bool k1 = (MODE == 1 && F.K == 1) || (MODE == 2 && G.K == 1);   // one set / one vector
     const int L4 = F.K >> 2;
     const bool em = MODE == 1 && !k1 && F.em && F.vec4 && (L4 > 32 ? L4 % 32 == 0 : 32 % L4 == 0);
     if constexpr (MODE == 1) {
