@@ -204,11 +204,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_spmv(RowRange rr, int K, const 
     for (int64_t i = r0 + (threadIdx.x >> 5); i < r1; i += wpb) {
         const int64_t a0 = rowptr[i] - rr.base, a1 = rowptr[i + 1] - rr.base;
         if (KS >= 32) {
-            for (int s0 = 0; s0 < K; s0 += 64) {
+            const int KK = KS == 64 ? 64 : K;                      // KS = 64: exactly 64 sets
+            for (int s0 = 0; s0 < KK; s0 += 64) {
                 const int sa = s0 + lane, sb = s0 + 32 + lane;
-                const bool ha = sa < K, hb = sb < K;
-                const float2 Xa = ha ? xm[i * K + sa] : make_float2(0.f, 0.f);
-                const float2 Xb = hb ? xm[i * K + sb] : make_float2(0.f, 0.f);
+                const bool ha = sa < KK, hb = sb < KK;
+                const float2 Xa = ha ? xm[i * KK + sa] : make_float2(0.f, 0.f);
+                const float2 Xb = hb ? xm[i * KK + sb] : make_float2(0.f, 0.f);
                 DF acc_a = df_of(0.f), acc_b = df_of(0.f);
                 int64_t k = a0;
                 for (; k + 3 < a1; k += 4) {
@@ -217,31 +218,31 @@ __global__ void __launch_bounds__(kThreads, 4) k_spmv(RowRange rr, int K, const 
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         c[u] = col[k + u];
-                        va[u] = ha ? vem[(k + u) * K + sa] : 0.f;
-                        vb[u] = hb ? vem[(k + u) * K + sb] : 0.f;
+                        va[u] = ha ? vem[(k + u) * KK + sa] : 0.f;
+                        vb[u] = hb ? vem[(k + u) * KK + sb] : 0.f;
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        if (ha) acc_a = df_add(acc_a, df_prod(va[u], xs[c[u] * K + sa]));
-                        if (hb) acc_b = df_add(acc_b, df_prod(vb[u], xs[c[u] * K + sb]));
+                        if (ha) acc_a = df_add(acc_a, df_prod(va[u], xs[c[u] * KK + sa]));
+                        if (hb) acc_b = df_add(acc_b, df_prod(vb[u], xs[c[u] * KK + sb]));
                         if (c[u] != i) {
-                            if (ha) mirror_add(yfix + c[u] * K + sa, df_prod(va[u], Xa));
-                            if (hb) mirror_add(yfix + c[u] * K + sb, df_prod(vb[u], Xb));
+                            if (ha) mirror_add(yfix + c[u] * KK + sa, df_prod(va[u], Xa));
+                            if (hb) mirror_add(yfix + c[u] * KK + sb, df_prod(vb[u], Xb));
                         }
                     }
                 }
                 for (; k < a1; ++k) {
                     const int64_t c = col[k];
-                    const float va = ha ? vem[k * K + sa] : 0.f, vb = hb ? vem[k * K + sb] : 0.f;
-                    if (ha) acc_a = df_add(acc_a, df_prod(va, xs[c * K + sa]));
-                    if (hb) acc_b = df_add(acc_b, df_prod(vb, xs[c * K + sb]));
+                    const float va = ha ? vem[k * KK + sa] : 0.f, vb = hb ? vem[k * KK + sb] : 0.f;
+                    if (ha) acc_a = df_add(acc_a, df_prod(va, xs[c * KK + sa]));
+                    if (hb) acc_b = df_add(acc_b, df_prod(vb, xs[c * KK + sb]));
                     if (c != i) {
-                        if (ha) mirror_add(yfix + c * K + sa, df_prod(va, Xa));
-                        if (hb) mirror_add(yfix + c * K + sb, df_prod(vb, Xb));
+                        if (ha) mirror_add(yfix + c * KK + sa, df_prod(va, Xa));
+                        if (hb) mirror_add(yfix + c * KK + sb, df_prod(vb, Xb));
                     }
                 }
-                if (ha) yrow[i * K + sa] = make_float2(acc_a.hi, acc_a.lo);
-                if (hb) yrow[i * K + sb] = make_float2(acc_b.hi, acc_b.lo);
+                if (ha) yrow[i * KK + sa] = make_float2(acc_a.hi, acc_a.lo);
+                if (hb) yrow[i * KK + sb] = make_float2(acc_b.hi, acc_b.lo);
             }
         } else {
             constexpr int G = 32 / KS;
@@ -325,7 +326,8 @@ void launch_spmv(RowRange rr, int K, const int64_t *rowptr, const int32_t *col, 
                  const float2 *xm, float2 *yrow, unsigned long long *yfix, int gr, cudaStream_t st)
 {
     count_launches(1);
-    if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    if (K == 64) k_spmv<64><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
+    else if (K >= 32) k_spmv<32><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
     else if (K == 1) k_spmv<1><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
     else if (K <= 2) k_spmv<2><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
     else if (K <= 4) k_spmv<4><<<gr, kThreads, 0, st>>>(rr, K, rowptr, col, vem, xs, xm, yrow, yfix);
