@@ -250,12 +250,14 @@ __device__ __forceinline__ void put_single(const DevBasis &B, const FillArgs &F,
 // warp: K/4 lanes copy one element's K values as float4s, so that a store
 // instruction covers whole lines.  Needs F.em, F.vec4 and K/4 dividing 32 or
 // a multiple of 32.  Columns are written by the caller.
+template <int KC>
 __device__ __forceinline__ void put_values_coop(const FillArgs &F, const RowOut &R, bool act, int idx, int sgn, int e)
 {
+    const int KK = KC > 0 ? KC : F.K;                          // KC > 0: the set count at compile time
     const int lane = threadIdx.x & 31;
     const unsigned am = __ballot_sync(0xffffffffu, act);
     if (!am) return;
-    const int L = F.K >> 2;                                      // float4s per element
+    const int L = KK >> 2;                                       // float4s per element
     const int last = 31 - __clz(am);
     if (L <= 32) {
         // four rounds of P elements at a time: the four table reads are in
@@ -277,7 +279,7 @@ __device__ __forceinline__ void put_values_coop(const FillArgs &F, const RowOut 
                 v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (on[u]) {
                     const int sm = js ? (int)0x80000000 : 0;
-                    v[u] = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)jidx * F.K) + q);
+                    v[u] = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)jidx * KK) + q);
                     v[u].x = __int_as_float(__float_as_int(v[u].x) ^ sm);
                     v[u].y = __int_as_float(__float_as_int(v[u].y) ^ sm);
                     v[u].z = __int_as_float(__float_as_int(v[u].z) ^ sm);
@@ -295,7 +297,7 @@ __device__ __forceinline__ void put_values_coop(const FillArgs &F, const RowOut 
             const int js = __shfl_sync(0xffffffffu, sgn, j);
             if (!((am >> j) & 1)) continue;
             const int sm = js ? (int)0x80000000 : 0;
-            const float4 *t4 = reinterpret_cast<const float4 *>(F.tbme + (int64_t)jidx * F.K);
+            const float4 *t4 = reinterpret_cast<const float4 *>(F.tbme + (int64_t)jidx * KK);
             float4 *o4 = reinterpret_cast<float4 *>(R.val + (int64_t)je * R.es);
             for (int q = lane; q < L; q += 32) {
                 float4 v = __ldg(t4 + q);
@@ -314,7 +316,7 @@ __device__ __forceinline__ void put_values_coop(const FillArgs &F, const RowOut 
 // kLaneSets sets on: one element at a time, lanes over sets).
 // The queue holds row-relative positions, columns and packed moves
 // (bra-only a, ket-only c, sign, neutron flag in bit 31).
-template <int MODE, bool K1, bool EM>
+template <int MODE, bool K1, int EM>
 __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, const FillArgs &F, const GradArgs &Gr,
                                            int *status, const int16_t *w_occ, const int32_t *w_spos,
                                            const int32_t *w_scol, const uint32_t *w_scode, int &nslow,
@@ -354,7 +356,8 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
             }
             __syncwarp();
             const int ne = min(per, ns - e0);
-            const int L4 = F.K >> 2;
+            const int KK = EM > 1 ? EM : F.K;                 // EM > 1: the set count at compile time
+            const int L4 = KK >> 2;
             if (EM) {
                 // element-major values: K/4 lanes per element with float4 reads and
                 // writes, 32 / (K/4) elements at a time; each set's sum in the same
@@ -376,7 +379,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
                     for (int i = 0; i < sp_n; ++i) {
                         const int2 q = sj[i];
                         if (q.x < 0) continue;
-                        float4 t = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)q.x * F.K) + q4);
+                        float4 t = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)q.x * KK) + q4);
                         if (q.y < 0) { t.x = -t.x; t.y = -t.y; t.z = -t.z; t.w = -t.w; }
                         v0 = df_add(v0, df_of(t.x));
                         v1 = df_add(v1, df_of(t.y));
@@ -388,10 +391,8 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
                     __stcs(reinterpret_cast<float4 *>(R.val + (int64_t)eo * R.es) + q4, r);
                     if (q4 == 0) R.col[eo] = w_scol[e];
                 }
-                __syncwarp();
-                continue;
             }
-            for (int j = 0; j < ne; ++j) {
+            for (int j = 0; j < (EM ? 0 : ne); ++j) {                // the other layouts: one element at a time
                 const int e = e0 + j;
                 const uint32_t code = w_scode[e];
                 const int base = (code >> 31) ? nbase : 0;
@@ -472,7 +473,7 @@ __device__ __forceinline__ void flush_slow(const DevBasis &B, const int2 *lg, co
     nslow = 0;
 }
 
-template <int W, int MODE, bool K1, int WARPS, bool EM>
+template <int W, int MODE, bool K1, int WARPS, int EM>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS)
 k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs Gr, int64_t r0, int64_t r1,
        int *status)
@@ -541,7 +542,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
         RowOut R;
         R.row = row;
         R.psir = (MODE == 2 && K1) ? Gr.psi[row] : 0;
-        R.es = (MODE == 1 && F.em) ? F.K : 1;
+        R.es = (MODE == 1 && F.em) ? (EM > 1 ? EM : F.K) : 1;
         R.ks = (MODE == 1 && F.em) ? 1 : nnz;
         int rowlen = 0;
         if (MODE == 1) {
@@ -579,7 +580,8 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     const float2 q = e1[w_occ[i]];
                     one = df_add(one, DF{q.x, q.y});
                 }
-                const int L4 = F.K >> 2;
+                const int KK = EM > 1 ? EM : F.K;
+                const int L4 = KK >> 2;
                 if (EM && L4 <= 32) {
                     // element-major values: four sets per lane, float4 reads, the same
                     // per-set order as below
@@ -589,7 +591,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                         for (int l = 0; l < npairs; ++l) {
                             const int32_t idx = w_scol[l];
                             if (idx < 0) continue;
-                            float4 t = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)idx * F.K) + q4);
+                            float4 t = __ldg(reinterpret_cast<const float4 *>(F.tbme + (int64_t)idx * KK) + q4);
                             if (w_scode[l]) { t.x = -t.x; t.y = -t.y; t.z = -t.z; t.w = -t.w; }
                             a0 = df_add(a0, df_of(t.x));
                             a1 = df_add(a1, df_of(t.y));
@@ -669,7 +671,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                     const int e = pos + __popc(bm & lt);
                     if (MODE == 1 && coop) {
                         if (in && !slow) __stcs(R.col + e, (int32_t)(cbp + y));
-                        put_values_coop(F, R, in && !slow, tb >> 1, tb & 1, e);
+                        put_values_coop<(EM > 1 ? EM : 0)>(F, R, in && !slow, tb >> 1, tb & 1, e);
                     } else if (in && !slow) {
                         put_single<MODE, K1>(B, F, Gr, R, e, cbp + y, tb >> 1, tb & 1);
                     }
@@ -726,8 +728,8 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                 if (MODE == 1 && coop) {
                     if (self0 && two0) __stcs(R.col + ex0, r0.x + n);
                     if (self1 && two1) __stcs(R.col + ex1, r1.x + n);
-                    put_values_coop(F, R, self0 && two0, (int)((uint32_t)r0.z >> 1), r0.z & 1, ex0);
-                    put_values_coop(F, R, self1 && two1, (int)((uint32_t)r1.z >> 1), r1.z & 1, ex1);
+                    put_values_coop<(EM > 1 ? EM : 0)>(F, R, self0 && two0, (int)((uint32_t)r0.z >> 1), r0.z & 1, ex0);
+                    put_values_coop<(EM > 1 ? EM : 0)>(F, R, self1 && two1, (int)((uint32_t)r1.z >> 1), r1.z & 1, ex1);
                 } else {
                     if (self0 && two0)
                         put_single<MODE, K1>(B, F, Gr, R, ex0, (int64_t)r0.x + n, (int)((uint32_t)r0.z >> 1), r0.z & 1);
@@ -795,7 +797,7 @@ k_rows(DevBasis B, const int64_t *rowptr, int64_t *counts, FillArgs F, GradArgs 
                             if (MODE == 1 && coop) __stcs(R.col + at, sg4.x + ent.x);
                             else put_single<MODE, K1>(B, F, Gr, R, at, (int64_t)(sg4.x + ent.x), idx, sg);
                         }
-                        if (MODE == 1 && coop) put_values_coop(F, R, e < Tpn, idx, sg, at);
+                        if (MODE == 1 && coop) put_values_coop<(EM > 1 ? EM : 0)>(F, R, e < Tpn, idx, sg, at);
                         before += __popc(mk);
                     }
                     __syncwarp();
@@ -909,14 +911,19 @@ int launch_rows_w(const cih_basis &b, const int64_t *rowptr, int64_t *counts, co
     const bool em = MODE == 1 && !k1 && F.em && F.vec4 && (L4 > 32 ? L4 % 32 == 0 : 32 % L4 == 0);
     if constexpr (MODE == 1) {
         if (em) {                                            // element-major K sets: warp-cooperative writes
-            if (b.W == 1) return go(k_rows<1, MODE, false, WARPS, true>);
-            if (b.W == 2) return go(k_rows<2, MODE, false, WARPS, true>);
-            return go(k_rows<4, MODE, false, WARPS, true>);
+            if (F.K == 64) {                                 // the batched configuration's set count
+                if (b.W == 1) return go(k_rows<1, MODE, false, WARPS, 64>);
+                if (b.W == 2) return go(k_rows<2, MODE, false, WARPS, 64>);
+                return go(k_rows<4, MODE, false, WARPS, 64>);
+            }
+            if (b.W == 1) return go(k_rows<1, MODE, false, WARPS, 1>);
+            if (b.W == 2) return go(k_rows<2, MODE, false, WARPS, 1>);
+            return go(k_rows<4, MODE, false, WARPS, 1>);
         }
     }
-    if (b.W == 1) return k1 ? go(k_rows<1, MODE, true, WARPS, false>) : go(k_rows<1, MODE, false, WARPS, false>);
-    if (b.W == 2) return k1 ? go(k_rows<2, MODE, true, WARPS, false>) : go(k_rows<2, MODE, false, WARPS, false>);
-    return k1 ? go(k_rows<4, MODE, true, WARPS, false>) : go(k_rows<4, MODE, false, WARPS, false>);
+    if (b.W == 1) return k1 ? go(k_rows<1, MODE, true, WARPS, 0>) : go(k_rows<1, MODE, false, WARPS, 0>);
+    if (b.W == 2) return k1 ? go(k_rows<2, MODE, true, WARPS, 0>) : go(k_rows<2, MODE, false, WARPS, 0>);
+    return k1 ? go(k_rows<4, MODE, true, WARPS, 0>) : go(k_rows<4, MODE, false, WARPS, 0>);
 }
 
 template <int MODE>
