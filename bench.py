@@ -39,6 +39,7 @@ WORKLOADS = {
     "3p3n_nmax6": dict(Z=3, N=3, Nmax=6, twoM=0, seed=100),
     "4p4n_nmax4": dict(Z=4, N=4, Nmax=4, twoM=0, seed=0),
     "3p3n_nmax2": dict(Z=3, N=3, Nmax=2, twoM=0, seed=0),
+    "3p4n_nmax4": dict(Z=3, N=4, Nmax=4, twoM=1, seed=0),   # 8.0 M stored nonzeros: mid-size ncu captures
 }
 FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_NNZ = 8            # int32 column + float32 value written by the fill
