@@ -197,3 +197,32 @@ def test_batched_lanczos(cih, built):
     assert abs(np.linalg.norm(p) - 1.0) < 1e-10
     del psi
     torch.cuda.empty_cache()
+
+
+def test_batched_four_word_strings_against_oracle(cih):
+    """The 64-set batched kernel on a space whose sub-determinants take four
+    64-bit words (3+3 Nmax=6: 60 M stored nonzeros, 15.4 GB of values):
+    sampled rows of the first and last set against the oracle."""
+    sp = (3, 3, 6, 0)
+    B = cih.Basis(*sp)
+    S = oracle.Space(*sp)
+    T = synth.tbme_tables(B.tbme_len, SEEDS)
+    til = cih.tbme_interleave(torch.from_numpy(T).cuda())
+    rowptr, nnz = B.count()
+    col, vem = B.fill_batched(rowptr, nnz, til, K)
+    B.check()
+    rp = rowptr.cpu().numpy()
+    rng = np.random.default_rng(9)
+    rows = np.unique(np.concatenate([rng.integers(0, B.dim, 40), [0, B.dim - 1]])).astype(np.int64)
+    c = col.cpu().numpy()
+    sel = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows])
+    v_sel = vem[torch.from_numpy(sel).cuda()].cpu().numpy()                 # (elements, K)
+    for k in (0, K - 1):
+        cnt, off, col_o, val_o = S.rows(rows, T[k])
+        np.testing.assert_array_equal(np.diff(rp)[rows], cnt)
+        np.testing.assert_array_equal(c[sel], col_o)
+        v = v_sel[:, k].astype(np.float64)
+        bad = np.abs(v - val_o) > 1e-5 * (np.abs(val_o) + 1.0)
+        assert not bad.any(), (k, int(bad.sum()))
+    del col, vem, til
+    torch.cuda.empty_cache()
