@@ -55,7 +55,7 @@ def test_autograd_fd_density_euler(cih):
     rowptr, col, val, nnz = cih.build_hamiltonian(B, t.detach().unsqueeze(0))
     ev, psi, conv = B.lanczos(rowptr, col, val, nev=1, max_iter=500, tol=1e-11)
     assert conv
-    assert float(e0) == ev[0][0]
+    assert float(e0.detach()) == ev[0][0]
     g = B.tbme_grad(rowptr, psi)[0].cpu().numpy()
     np.testing.assert_array_equal(g32, g.astype(np.float32))
     assert np.all(np.abs(g) <= 2.0 + 1e-12)
