@@ -4,8 +4,11 @@
 //
 // Device:
 //   - y = H x reads each stored nonzero of the upper half once: the row part
-//     in FP64 registers, the mirrored half added to 64-bit fixed-point column
-//     accumulators (integer atomic adds commute, so y is deterministic);
+//     as double-float sums of FP32-pair products, the mirrored half added to
+//     64-bit fixed-point column accumulators (integer atomic adds commute, so
+//     y is deterministic); no FP64 operation per nonzero;
+//   - over row shards held by several processes, each multiplies its own rows
+//     and a caller callback sums the two product buffers across them;
 //   - values element-major (the K values of a nonzero together) and vectors
 //     element-major x[i * K + s], FP64;
 //   - full reorthogonalisation: classical Gram-Schmidt applied twice, dot
@@ -63,8 +66,8 @@ struct RowRange {
 
 // ---- y = H x from the stored upper half, each stored nonzero read once.
 //
-// Row i's warp forms the row part sum_j h_ij x_j in FP64 registers (a fixed
-// order: lanes, then a shuffle tree), and sends each strictly-upper h_ij x_i
+// Row i's warp forms the row part sum_j h_ij x_j (double-float sums in a
+// fixed order: lanes, then a shuffle tree), and sends each strictly-upper h_ij x_i
 // to column j's accumulator as a 64-bit fixed-point integer (units 2^-s) by
 // an atomic add.  Integer adds commute, so y does not depend on the order in
 // which rows run: the product is deterministic without a transposed copy.
@@ -73,8 +76,8 @@ struct RowRange {
 // The scale 2^s keeps every accumulator inside 2^60: for column j,
 // |sum_{i<j} h_ij x_i| <= ||h_{.j}|| ||x|| (Cauchy-Schwarz) <= F ||x||, with
 // F the Frobenius norm of the strictly-upper part over all sets, and the
-// Lanczos vectors have ||x|| = 1.  Products are rounded to the nearest unit,
-// so each one carries at most 2^-s-1 of absolute error.
+// Lanczos vectors have ||x|| = 1.  Each product, an FP32 pair, enters as its
+// rounded hi plus its rounded lo: at most one unit 2^-s of absolute error.
 
 // partial[blk] = this block's sum of the squares of the strictly-upper
 // values of all sets (a warp per row, lanes over (nonzero, set) pairs), in
