@@ -103,7 +103,7 @@ __device__ __forceinline__ long long psi_prod(const long long *psi, int64_t i, i
 // Warps walk rows independently (grid-stride); a CTA only shares the pn
 // split table S in shared memory.  For row (p, n):
 //   diagonal  - the warp sums the one-body energies and every occupied pair
-//               (lanes over pairs, FP64 reduction);
+//               (lanes over pairs, double-float reduction);
 //   A         - n's forward same-class neighbours inside p's partner range:
 //               two-moves from their precomputed table index, one-moves
 //               deferred;
@@ -115,7 +115,7 @@ __device__ __forceinline__ long long psi_prod(const long long *psi, int64_t i, i
 //               index, pn elements u(a,b) = S[a][kappa] + r(b), proton
 //               one-moves are deferred;
 //   deferred  - one-move elements, lanes over (element, spectator) pairs and
-//               a segmented FP64 reduction.
+//               a segmented double-float reduction (K sets: lanes over sets).
 
 constexpr int kLaneSets = 16;     // from this many sets on, multi-term sums run with lanes over sets
 constexpr int kSlowCap = 64;
