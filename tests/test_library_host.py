@@ -155,6 +155,12 @@ def test_entry_points_reject_bad_arguments_without_a_gpu(cih):
                                      None, None) == -1
     assert lib.cih_ham_spmv(h, C.c_void_p(16), C.c_void_p(16), C.c_void_p(16), 1, 0, C.c_void_p(16),
                             C.c_void_p(24), None) == -1
+    f2 = C.c_double()
+    assert lib.cih_ham_upper_sumsq(h, C.c_void_p(16), 0, 1, C.c_void_p(16), 1, 0, C.byref(f2), None) == -1
+    noop = lib.cih_lanczos_lowest_shard.argtypes[14](lambda ctx: 0)
+    assert lib.cih_lanczos_lowest_shard(h, C.c_void_p(16), 0, 1, C.c_void_p(16), C.c_void_p(16), 1, 0, 1, 10,
+                                        1e-8, 1.0, C.c_void_p(16), C.c_void_p(24), noop, None, ev, None,
+                                        None) == -1
     w, c, ms = C.c_int32(), C.c_int32(), C.c_float()
     assert lib.cih_autotune_fill(h, C.c_void_p(16), 1, 20.0, C.c_void_p(16), 0, None, C.c_void_p(16),
                                  C.c_void_p(16), None, C.byref(w), C.byref(c), C.byref(ms)) == -1
